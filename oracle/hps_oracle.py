@@ -1,0 +1,453 @@
+"""FP64 CPU oracle for the HPS leaf static condensation, merge and solve.
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain, obviously correct
+statement of what the GPU library computes.  Only the test-suite, the smoke
+check and the CPU-baseline leg of the benchmark may import or run it; the
+product path (the CUDA library and its Python binding) never does, and this
+module imports nothing from the product package.  Coefficients, body loads
+and boundary data are passed in as arrays; the seeded workload generators
+live elsewhere and hold none of the arithmetic below.
+
+Everything is float64 numpy, with LAPACK (scipy.linalg.lu_factor/lu_solve)
+and numpy.linalg.solve as the only library primitives.
+
+Paper: Yesypenko & Martinsson, "GPU Optimizations for the Hierarchical
+Poincare-Steklov Scheme" (arXiv 2211.14969).  Citations below are to its
+sections and equations:
+
+* Eq. (bvp), Eq. (var_helm): the BVP  A u = f in Omega, u = g on dOmega,
+  with A u = -Lap u - kappa^2 b(x) u.
+* Section 2: p x p tensor mesh of Chebyshev points per leaf, spectral
+  collocation of the PDE at interior nodes, flux continuity on element
+  boundaries, static condensation of the interior nodes leaving the reduced
+  system of Eq. (hps_reduced) on the leaf edges.
+* Section 2 Remark: leaf factorizations are re-formed after the reduced solve.
+* Eq. (chain_rule): the general second-order form with mixed derivative,
+  which fixes the "2 c12 d^2/dx1dx2" convention of the operator here.
+* Eq. (accuracy_formula): relerr_res and relerr_true.
+
+The paper defers the formulas of the leaf solution operator, the
+Dirichlet-to-Neumann (DtN) map and the merge to its references
+[babb2018accelerated, 2019_martinsson_book, hao2016direct]; the standard
+forms are used:  S = -A_ii^{-1} A_ib,  T = N_b + N_i S,  and the merge of two
+boxes as a Schur complement on their shared edge.
+
+Readings where the paper is silent (each is also listed in the design notes):
+* p is the number of Chebyshev points per direction (degree p-1).
+* Leaf corners are not unknowns.  With c12 == 0 no interior or normal row
+  touches a corner, so dropping them is exact; rows of a c12 != 0 operator
+  that touch a corner are not condensed here (parity unpinned for c12 != 0
+  condensation; assembly with c12 != 0 is pinned).
+* Node id i*p + j, i the x index; interior nodes lexicographic (i major);
+  boundary order [W, E, S, N], each edge by increasing coordinate.
+* Normal rows use the outward normal: -d/dx on W, +d/dx on E, -d/dy on S,
+  +d/dy on N, so flux continuity across an interface is "sum == 0".
+* Merges alternate x then y (x first), siblings ordered west/east or
+  south/north; the parent boundary is again [W, E, S, N] by increasing
+  coordinate.
+"""
+
+import numpy as np
+import scipy.linalg as sla
+
+# ----------------------------------------------------------------------------
+# Chebyshev grid and differentiation  (Section 2: "p x p tensor product mesh of
+# Chebyshev points", "spectral differentiation")
+# ----------------------------------------------------------------------------
+
+
+def cheb_points(p):
+    """The p Chebyshev-Gauss-Lobatto points on [-1, 1] in increasing order."""
+    k = np.arange(p, dtype=np.float64)
+    return -np.cos(np.pi * k / (p - 1))
+
+
+def cheb_diff(p):
+    """Chebyshev spectral differentiation matrix on cheb_points(p).
+
+    Textbook definition (Trefethen, Spectral Methods in MATLAB, ch. 6):
+    off-diagonal D[i, j] = (c_i / c_j) (-1)^(i+j) / (t_i - t_j) with
+    c_0 = c_{p-1} = 2 and c_k = 1 otherwise; the diagonal is minus the row sum
+    of the off-diagonal entries (D applied to a constant is zero).
+    """
+    t = cheb_points(p)
+    c = np.ones(p)
+    c[0] = 2.0
+    c[-1] = 2.0
+    D = np.zeros((p, p))
+    for i in range(p):
+        for j in range(p):
+            if i != j:
+                D[i, j] = (c[i] / c[j]) * (-1.0) ** (i + j) / (t[i] - t[j])
+    for i in range(p):
+        D[i, i] = -(D[i, :].sum() - D[i, i])
+    return D
+
+
+def leaf_nodes(p, box):
+    """Node coordinates (x, y), each of length p*p, node id i*p + j.
+
+    box = (x0, y0, hx, hy); x_i = x0 + (1 + t_i) hx / 2, likewise y_j.
+    """
+    x0, y0, hx, hy = box
+    t = cheb_points(p)
+    xs = x0 + (1.0 + t) * hx / 2.0
+    ys = y0 + (1.0 + t) * hy / 2.0
+    X = np.repeat(xs, p)   # x index i is the slow one
+    Y = np.tile(ys, p)
+    return X, Y
+
+
+def leaf_index_sets(p):
+    """Interior set I and boundary edges W, E, S, N (corners dropped)."""
+    q = range(1, p - 1)
+    I = [i * p + j for i in q for j in q]
+    W = [0 * p + j for j in q]
+    E = [(p - 1) * p + j for j in q]
+    S = [i * p + 0 for i in q]
+    N = [i * p + (p - 1) for i in q]
+    return {"I": I, "W": W, "E": E, "S": S, "N": N, "B": W + E + S + N}
+
+
+def leaf_operator(p, box, coef, kappa):
+    """Full p^2 x p^2 collocation matrix of the leaf and its normal rows.
+
+    coef is a (6, p*p) array of (c11, c12, c22, c1, c2, b) at the leaf nodes.
+    The operator is the variable-coefficient Helmholtz operator of
+    Eq. (var_helm) in the general form of Eq. (chain_rule):
+        A u = -(c11 u_xx + 2 c12 u_xy + c22 u_yy + c1 u_x + c2 u_y)
+              - kappa^2 b u,
+    with the derivatives replaced by Kronecker products of the 1D Chebyshev
+    matrix scaled to the leaf (Section 2).  Returns (A, Nrow, Dx, Dy), where
+    Nrow (n_b x p^2) holds the outward normal derivative at the boundary
+    nodes in [W, E, S, N] order.
+    """
+    x0, y0, hx, hy = box
+    D = cheb_diff(p)
+    Ip = np.eye(p)
+    Dx = np.kron((2.0 / hx) * D, Ip)   # acts on the x index i of id i*p+j
+    Dy = np.kron(Ip, (2.0 / hy) * D)   # acts on the y index j
+    c11, c12, c22, c1, c2, b = (np.asarray(c, dtype=np.float64) for c in coef)
+    A = -(c11[:, None] * (Dx @ Dx)
+          + 2.0 * c12[:, None] * (Dx @ Dy)
+          + c22[:, None] * (Dy @ Dy)
+          + c1[:, None] * Dx
+          + c2[:, None] * Dy)
+    A = A - kappa ** 2 * np.diag(b)
+    ix = leaf_index_sets(p)
+    Nrow = np.vstack([-Dx[ix["W"]], Dx[ix["E"]], -Dy[ix["S"]], Dy[ix["N"]]])
+    return A, Nrow, Dx, Dy
+
+
+# ----------------------------------------------------------------------------
+# Leaf static condensation  (Section 2: eliminate the interior nodes of each
+# leaf with dense LU and matrix-matrix products)
+# ----------------------------------------------------------------------------
+
+
+def condense_leaf(p, box, coef, kappa, f=None):
+    """Condense one leaf.
+
+    f is the body load at the p*p nodes, shape (p*p, m) (or None for m = 0).
+    Returns a dict with
+        S (n_i x n_b) = -A_ii^{-1} A_ib     solution operator,
+        T (n_b x n_b) = N_b + N_i S         DtN map,
+        W (n_i x m)   = A_ii^{-1} f_I       particular interior solution,
+        h (n_b x m)   = N_i W               its outgoing flux,
+    and the blocks used (A_ii, A_ib, N_b, N_i) for diagnostics.
+    With u_i = S u_b + W on the leaf, the outgoing flux is T u_b + h.
+    """
+    A, Nrow, _, _ = leaf_operator(p, box, coef, kappa)
+    ix = leaf_index_sets(p)
+    I, B = ix["I"], ix["B"]
+    A_ii = A[np.ix_(I, I)]
+    A_ib = A[np.ix_(I, B)]
+    N_b = Nrow[:, B]
+    N_i = Nrow[:, I]
+    lu = sla.lu_factor(A_ii)
+    S = -sla.lu_solve(lu, A_ib)
+    T = N_b + N_i @ S
+    out = {"S": S, "T": T, "A_ii": A_ii, "A_ib": A_ib, "N_b": N_b, "N_i": N_i}
+    if f is not None:
+        f = np.asarray(f, dtype=np.float64).reshape(p * p, -1)
+        W = sla.lu_solve(lu, f[I])
+        out["W"] = W
+        out["h"] = N_i @ W
+    return out
+
+
+def leaf_interior_solve(S, W, u_b):
+    """Interior values from boundary values: u_i = S u_b + W (Section 2 Remark)."""
+    u_b = np.asarray(u_b).reshape(S.shape[1], -1)
+    return S @ u_b + (0.0 if W is None else W)
+
+
+# ----------------------------------------------------------------------------
+# Uniform grids of leaves: edge-node keys, merges and the downward solve
+# ----------------------------------------------------------------------------
+#
+# An edge node is named by a key (kind, line, seg, k):
+#   kind 'v': the vertical grid line x = line * hx, seg = leaf row iy,
+#   kind 'h': the horizontal grid line y = line * hy, seg = leaf column ix,
+#   k = 0 .. p-3 along the edge by increasing coordinate.
+
+
+def grid_boxes(nx, ny, x0=0.0, y0=0.0, lx=1.0, ly=1.0):
+    """Leaf boxes of an nx x ny tiling, leaf index ix * ny + iy."""
+    hx, hy = lx / nx, ly / ny
+    return [(x0 + ix * hx, y0 + iy * hy, hx, hy) for ix in range(nx) for iy in range(ny)]
+
+
+def box_keys(p, ix0, iy0, wx, wy):
+    """Boundary keys of the box of leaves [ix0, ix0+wx) x [iy0, iy0+wy), [W, E, S, N]."""
+    ks = range(p - 2)
+    W = [("v", ix0, iy, k) for iy in range(iy0, iy0 + wy) for k in ks]
+    E = [("v", ix0 + wx, iy, k) for iy in range(iy0, iy0 + wy) for k in ks]
+    S = [("h", iy0, ix, k) for ix in range(ix0, ix0 + wx) for k in ks]
+    N = [("h", iy0 + wy, ix, k) for ix in range(ix0, ix0 + wx) for k in ks]
+    return W + E + S + N
+
+
+def merge_schedule(nx, ny):
+    """Merge directions bottom-up: 'x' first, then alternate; one direction
+    continues alone once the other spans the grid.  nx, ny powers of two."""
+    for n in (nx, ny):
+        if n < 1 or (n & (n - 1)):
+            raise ValueError("merge tree needs power-of-two leaf counts")
+    wx, wy, out = 1, 1, []
+    while wx < nx or wy < ny:
+        if wx < nx and (wx <= wy or wy == ny):
+            out.append("x")
+            wx *= 2
+        else:
+            out.append("y")
+            wy *= 2
+    return out
+
+
+def merge_two(ka, Ta, ha, kb, Tb, hb, kpar):
+    """Merge sibling boxes alpha and beta along their shared edge (Schur
+    complement; the merge the paper defers to its HPS references).
+
+    ka, kb, kpar: boundary key lists; T*, h*: DtN maps and outgoing fluxes in
+    those orders.  With 1 = alpha's exterior, 2 = beta's exterior, 3 = shared:
+        Z  = Ta33 + Tb33
+        S3 = -Z^{-1} [Ta31  Tb32],   w3 = -Z^{-1} (ha3 + hb3)
+        T  = diag(Ta11, Tb22) + [Ta13; Tb23] S3
+        h  = [ha1; hb2] + [Ta13; Tb23] w3
+    T and h are returned in kpar order, S3 maps [u1; u2] (in the order
+    `k12`) to the shared-edge values (in the order `k3`).
+    """
+    pa = {k: i for i, k in enumerate(ka)}
+    pb = {k: i for i, k in enumerate(kb)}
+    k3 = [k for k in ka if k in pb]
+    k1 = [k for k in ka if k not in pb]
+    k2 = [k for k in kb if k not in pa]
+    a1 = [pa[k] for k in k1]
+    a3 = [pa[k] for k in k3]
+    b2 = [pb[k] for k in k2]
+    b3 = [pb[k] for k in k3]
+    Z = Ta[np.ix_(a3, a3)] + Tb[np.ix_(b3, b3)]
+    rhs = np.hstack([Ta[np.ix_(a3, a1)], Tb[np.ix_(b3, b2)]])
+    lu = sla.lu_factor(Z)
+    S3 = -sla.lu_solve(lu, rhs)
+    w3 = -sla.lu_solve(lu, ha[a3] + hb[b3])
+    n1, n2 = len(k1), len(k2)
+    T12 = np.zeros((n1 + n2, n1 + n2))
+    T12[:n1, :n1] = Ta[np.ix_(a1, a1)]
+    T12[n1:, n1:] = Tb[np.ix_(b2, b2)]
+    C = np.vstack([Ta[np.ix_(a1, a3)], Tb[np.ix_(b2, b3)]])
+    T12 = T12 + C @ S3
+    h12 = np.vstack([ha[a1], hb[b2]]) + C @ w3
+    k12 = k1 + k2
+    pos = {k: i for i, k in enumerate(k12)}
+    perm = [pos[k] for k in kpar]
+    if sorted(perm) != list(range(n1 + n2)):
+        raise AssertionError("parent keys are not the exterior of the children")
+    T = T12[np.ix_(perm, perm)]
+    h = h12[perm]
+    return {"T": T, "h": h, "S3": S3, "w3": w3, "k12": k12, "k3": k3}
+
+
+def hps_upward(p, nx, ny, leaves):
+    """Bottom-up merges over an nx x ny grid of condensed leaves.
+
+    leaves[ix * ny + iy] holds the leaf's T and h.  Returns the list of levels;
+    each level is a dict mapping the box origin (ix0, iy0) to its record.
+    """
+    boxes = {}
+    for ix in range(nx):
+        for iy in range(ny):
+            lf = leaves[ix * ny + iy]
+            boxes[(ix, iy)] = {"T": lf["T"], "h": lf["h"], "keys": box_keys(p, ix, iy, 1, 1)}
+    wx, wy = 1, 1
+    levels = []
+    for d in merge_schedule(nx, ny):
+        new = {}
+        for (ix0, iy0) in sorted(boxes):
+            if d == "x" and (ix0 // wx) % 2 == 0:
+                a, b = boxes[(ix0, iy0)], boxes[(ix0 + wx, iy0)]
+                kpar = box_keys(p, ix0, iy0, 2 * wx, wy)
+            elif d == "y" and (iy0 // wy) % 2 == 0:
+                a, b = boxes[(ix0, iy0)], boxes[(ix0, iy0 + wy)]
+                kpar = box_keys(p, ix0, iy0, wx, 2 * wy)
+            else:
+                continue
+            rec = merge_two(a["keys"], a["T"], a["h"], b["keys"], b["T"], b["h"], kpar)
+            rec["keys"] = kpar
+            rec["children"] = ((ix0, iy0), (ix0 + wx, iy0) if d == "x" else (ix0, iy0 + wy))
+            new[(ix0, iy0)] = rec
+        if d == "x":
+            wx *= 2
+        else:
+            wy *= 2
+        boxes = new
+        levels.append(new)
+    return levels
+
+
+def hps_downward(p, nx, ny, levels, leaves, g_keys):
+    """Top-down solve (Section 2 Remark: leaf values after the reduced solve).
+
+    g_keys: dict key -> Dirichlet value(s) (shape (m,)) on the outer boundary.
+    Returns per leaf the boundary values u_b (n_b x m) and interior values
+    u_i (n_i x m) = S u_b + W.
+    """
+    vals = dict(g_keys)
+    for lev in reversed(levels):
+        for rec in lev.values():
+            u12 = np.array([vals[k] for k in rec["k12"]])
+            u3 = rec["S3"] @ u12 + rec["w3"]
+            for k, v in zip(rec["k3"], u3):
+                vals[k] = v
+    out = []
+    for ix in range(nx):
+        for iy in range(ny):
+            lf = leaves[ix * ny + iy]
+            ub = np.array([vals[k] for k in box_keys(p, ix, iy, 1, 1)])
+            ui = lf["S"] @ ub + lf["W"]
+            out.append({"u_b": ub, "u_i": ui})
+    return out
+
+
+def outer_boundary_keys(p, nx, ny):
+    return box_keys(p, 0, 0, nx, ny)
+
+
+def key_coords(p, key, nx, ny, lx=1.0, ly=1.0, x0=0.0, y0=0.0):
+    """Physical coordinate of an edge node named by its key."""
+    kind, line, seg, k = key
+    t = cheb_points(p)[1:-1]
+    hx, hy = lx / nx, ly / ny
+    if kind == "v":
+        return x0 + line * hx, y0 + seg * hy + (1.0 + t[k]) * hy / 2.0
+    return x0 + seg * hx + (1.0 + t[k]) * hx / 2.0, y0 + line * hy
+
+
+# ----------------------------------------------------------------------------
+# Brute-force global collocation system (Eq. (Au=f)), independent of merges
+# ----------------------------------------------------------------------------
+
+
+def global_system(p, nx, ny, coefs, kappa, f, g_fn, lx=1.0, ly=1.0):
+    """Assemble the global collocation system on an nx x ny leaf grid.
+
+    Unknowns: every leaf-interior node, then every edge node not on the outer
+    boundary.  Rows: the PDE at every leaf-interior node; flux continuity
+    (sum of the two leaves' outward normal derivatives = 0) at every
+    interface edge node.  Outer edge nodes carry Dirichlet data g and are
+    moved to the right-hand side.  coefs[l] is (6, p*p), f[l] is (p*p, m).
+    Returns (A, rhs, layout) with layout describing the unknown ordering.
+    """
+    boxes = grid_boxes(nx, ny, lx=lx, ly=ly)
+    ix_sets = leaf_index_sets(p)
+    I, B = ix_sets["I"], ix_sets["B"]
+    n_i, n_b = len(I), len(B)
+    nl = nx * ny
+    m = np.asarray(f[0]).reshape(p * p, -1).shape[1]
+    # edge keys
+    outer = set(outer_boundary_keys(p, nx, ny))
+    iface = []
+    seen = set()
+    for ix in range(nx):
+        for iy in range(ny):
+            for k in box_keys(p, ix, iy, 1, 1):
+                if k not in outer and k not in seen:
+                    seen.add(k)
+                    iface.append(k)
+    kid = {k: nl * n_i + i for i, k in enumerate(iface)}
+    n = nl * n_i + len(iface)
+    A = np.zeros((n, n))
+    rhs = np.zeros((n, m))
+    gvals = {}
+    for k in outer:
+        gvals[k] = np.atleast_1d(g_fn(*key_coords(p, k, nx, ny, lx, ly)))
+    corners = [0, p - 1, (p - 1) * p, p * p - 1]
+    for l, box in enumerate(boxes):
+        ix, iy = divmod(l, ny)
+        Al, Nrow, _, _ = leaf_operator(p, box, coefs[l], kappa)
+        keys = box_keys(p, ix, iy, 1, 1)
+        # local node -> ('u', col) or ('g', key)
+        colmap = {}
+        for q, node in enumerate(I):
+            colmap[node] = ("u", l * n_i + q)
+        for q, node in enumerate(B):
+            k = keys[q]
+            colmap[node] = ("g", k) if k in outer else ("u", kid[k])
+        fl = np.asarray(f[l]).reshape(p * p, m)
+
+        def put(row, coeffs, target_rhs_sign=1.0):
+            for node in range(p * p):
+                a = coeffs[node]
+                if a == 0.0:
+                    continue
+                if node in corners:
+                    raise NotImplementedError("operator row touches a leaf corner (c12 != 0)")
+                kind, c = colmap[node]
+                if kind == "u":
+                    A[row, c] += a
+                else:
+                    rhs[row] -= a * gvals[c]
+
+        for q, node in enumerate(I):
+            row = l * n_i + q
+            put(row, Al[node])
+            rhs[row] += fl[node]
+        for q in range(n_b):
+            k = keys[q]
+            if k in outer:
+                continue
+            put(kid[k], Nrow[q])
+    layout = {"n_i": n_i, "iface": iface, "kid": kid, "gvals": gvals}
+    return A, rhs, layout
+
+
+def global_dense_solve(p, nx, ny, coefs, kappa, f, g_fn, lx=1.0, ly=1.0):
+    """Solve the global system with numpy.linalg.solve; returns per-leaf
+    (u_b, u_i) in the same form as hps_downward, plus relerr_res of
+    Eq. (accuracy_formula) for the computed solution."""
+    A, rhs, lay = global_system(p, nx, ny, coefs, kappa, f, g_fn, lx, ly)
+    u = np.linalg.solve(A, rhs)
+    res = np.linalg.norm(A @ u - rhs) / np.linalg.norm(rhs)
+    n_i = lay["n_i"]
+    out = []
+    for ix in range(nx):
+        for iy in range(ny):
+            l = ix * ny + iy
+            ub = []
+            for k in box_keys(p, ix, iy, 1, 1):
+                ub.append(lay["gvals"][k] if k in lay["gvals"] else u[lay["kid"][k]])
+            out.append({"u_b": np.array(ub), "u_i": u[l * n_i:(l + 1) * n_i]})
+    return out, res
+
+
+# ----------------------------------------------------------------------------
+# Error metrics (Eq. (accuracy_formula))
+# ----------------------------------------------------------------------------
+
+
+def relerr(calc, ref):
+    """||calc - ref||_2 / ||ref||_2 (Frobenius for matrices)."""
+    calc = np.asarray(calc, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm(calc - ref) / np.linalg.norm(ref))

@@ -1,0 +1,327 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by
+mathematics (not against the oracle itself).
+
+* exact spectral differentiation of polynomials of degree <= p-1 (Section 2),
+  closed-form Chebyshev matrix entries and the hand-derived p = 2, 3 matrices
+  in tests/golden;
+* manufactured tensor-polynomial solutions: the collocated operator, the leaf
+  condensation (S, T, W, h) and the full merge + solve reproduce them to
+  rounding, for any wavenumber and coefficient samples;
+* the brute-force dense global collocation solve of Eq. (Au=f) agrees with
+  the merge tree;
+* plane-wave and J0 closed-form Helmholtz solutions (Section 3, Eq.
+  (constant_coeff_helm)) converge spectrally in p, and T maps a plane wave's
+  boundary trace to its normal derivative;
+* planted mistakes (a transposed D, a flipped normal, a dropped term, a wrong
+  merge key order) make at least one pin fail.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import scipy.special
+
+import oracle.hps_oracle as O
+from manufactured import TensorPoly, random_coef, random_poly
+from paper_2211_14969_b300 import workloads as WL
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS = np.finfo(np.float64).eps
+
+
+# ---------------------------------------------------------------- pin helpers
+
+def deriv_error(p):
+    """max relative error of D applied to Chebyshev polynomials T_k, k < p."""
+    t = O.cheb_points(p)
+    D = O.cheb_diff(p)
+    worst = 0.0
+    for k in range(p):
+        c = np.zeros(k + 1)
+        c[k] = 1.0
+        u = np.polynomial.chebyshev.chebval(t, c)
+        du = np.polynomial.chebyshev.chebval(t, np.polynomial.chebyshev.chebder(c)) if k else 0 * t
+        scale = max(1.0, np.abs(du).max())
+        worst = max(worst, np.abs(D @ u - du).max() / scale)
+    return worst
+
+
+def operator_error(p, box, coef, kappa, u):
+    x, y = O.leaf_nodes(p, box)
+    A, _, _, _ = O.leaf_operator(p, box, coef, kappa)
+    uv = u(x, y)
+    f = u.apply_operator(x, y, coef, kappa)
+    scale = np.abs(A) @ np.abs(uv)
+    return np.max(np.abs(A @ uv - f) / scale)
+
+
+def condense_errors(p, box, coef, kappa, u):
+    x, y = O.leaf_nodes(p, box)
+    f = u.apply_operator(x, y, coef, kappa)[:, None]
+    out = O.condense_leaf(p, box, coef, kappa, f)
+    ix = O.leaf_index_sets(p)
+    uv = u(x, y)
+    ub = uv[ix["B"]][:, None]
+    ui = uv[ix["I"]][:, None]
+    # analytic outward normal derivative on [W, E, S, N]
+    dudx = u(x, y, 1, 0)
+    dudy = u(x, y, 0, 1)
+    dn = np.concatenate([-dudx[ix["W"]], dudx[ix["E"]], -dudy[ix["S"]], dudy[ix["N"]]])[:, None]
+    e_int = O.relerr(out["S"] @ ub + out["W"], ui)
+    e_flux = O.relerr(out["T"] @ ub + out["h"], dn)
+    cond = np.linalg.cond(out["A_ii"])
+    return e_int, e_flux, cond
+
+
+def hps_grid_solve(p, nx, ny, coefs, kappa, f, g_fn):
+    boxes = O.grid_boxes(nx, ny)
+    leaves = [O.condense_leaf(p, boxes[l], coefs[l], kappa, f[l]) for l in range(nx * ny)]
+    levels = O.hps_upward(p, nx, ny, leaves)
+    gk = {k: np.atleast_1d(g_fn(*O.key_coords(p, k, nx, ny))) for k in O.outer_boundary_keys(p, nx, ny)}
+    return O.hps_downward(p, nx, ny, levels, leaves, gk), leaves
+
+
+def nodal_values(p, nx, ny, fn):
+    """Per leaf (u_b, u_i) of a function sampled at the leaf nodes."""
+    ix = O.leaf_index_sets(p)
+    out = []
+    for box in O.grid_boxes(nx, ny):
+        x, y = O.leaf_nodes(p, box)
+        v = fn(x, y)
+        out.append((v[ix["B"]], v[ix["I"]]))
+    return out
+
+
+def grid_error(sol, ref):
+    num = den = 0.0
+    for s, (rb, ri) in zip(sol, ref):
+        num += np.sum((s["u_b"].ravel() - rb.ravel()) ** 2) + np.sum((s["u_i"].ravel() - ri.ravel()) ** 2)
+        den += np.sum(rb ** 2) + np.sum(ri ** 2)
+    return np.sqrt(num / den)
+
+
+def manufactured_grid_error(p=8, nx=4, ny=4, kappa=7.0, seed=11):
+    rng = np.random.default_rng(seed)
+    u = random_poly(rng, p - 1, p - 1, xc=0.5, yc=0.5, sx=0.5, sy=0.5)
+    coefs, fs = [], []
+    for box in O.grid_boxes(nx, ny):
+        x, y = O.leaf_nodes(p, box)
+        c = random_coef(rng, p * p)
+        coefs.append(c)
+        fs.append(u.apply_operator(x, y, c, kappa)[:, None])
+    sol, _ = hps_grid_solve(p, nx, ny, coefs, kappa, fs, lambda x, y: u(x, y))
+    return grid_error(sol, nodal_values(p, nx, ny, u))
+
+
+# ------------------------------------------------------------------ the pins
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_cheb_diff_golden(p):
+    ref = np.loadtxt(os.path.join(GOLDEN, f"cheb_D_p{p}.txt"))
+    assert np.allclose(O.cheb_diff(p), ref, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [4, 6, 10, 12, 16, 20, 24, 30, 32, 42])
+def test_cheb_diff_exact_on_polynomials(p):
+    assert deriv_error(p) < 1e-13 * p * p
+
+
+@pytest.mark.parametrize("p", [5, 10, 20, 32])
+def test_cheb_diff_corner_closed_form(p):
+    n = p - 1
+    D = O.cheb_diff(p)
+    assert np.isclose(D[-1, -1], (2 * n * n + 1) / 6.0, rtol=1e-13)
+    assert np.isclose(D[0, 0], -(2 * n * n + 1) / 6.0, rtol=1e-13)
+
+
+def test_leaf_nodes_layout():
+    p, box = 5, (0.25, 0.5, 0.5, 0.25)
+    x, y = O.leaf_nodes(p, box)
+    # node id i*p + j, i the x index; endpoints of the box are nodes
+    assert x[0] == 0.25 and np.isclose(x[(p - 1) * p], 0.75)
+    assert y[0] == 0.5 and np.isclose(y[p - 1], 0.75)
+    assert np.all(np.diff(x[::p]) > 0) and np.all(np.diff(y[:p]) > 0)
+    ix = O.leaf_index_sets(10)
+    assert len(ix["I"]) == 64 and len(ix["B"]) == 32   # p = 10: 64 interior, 32 edge nodes
+    corners = {0, 9, 90, 99}
+    assert not corners & set(ix["B"]) and not corners & set(ix["I"])
+
+
+@pytest.mark.parametrize("p,c12", [(6, False), (10, True), (16, True), (20, False)])
+def test_operator_manufactured(p, c12):
+    rng = np.random.default_rng(p)
+    box = (0.3, -0.2, 0.125, 0.25)
+    u = random_poly(rng, p - 1, p - 1, xc=0.3625, yc=-0.075, sx=0.0625, sy=0.125)
+    coef = random_coef(rng, p * p, c12=c12)
+    assert operator_error(p, box, coef, 13.0, u) < 1e-12
+
+
+@pytest.mark.parametrize("p,kappa", [(6, 3.0), (10, 20.0), (14, 40.0), (20, 200.0 / 8)])
+def test_condense_manufactured(p, kappa):
+    rng = np.random.default_rng(100 + p)
+    box = (0.5, 0.25, 0.125, 0.0625)
+    u = random_poly(rng, p - 1, p - 1, xc=0.5625, yc=0.28125, sx=0.0625, sy=0.03125)
+    coef = random_coef(rng, p * p)
+    e_int, e_flux, cond = condense_errors(p, box, coef, kappa, u)
+    tol = max(1e-12, 100 * cond * EPS)
+    assert e_int < tol, (e_int, cond)
+    assert e_flux < tol, (e_flux, cond)
+
+
+def test_hps_merge_solve_manufactured():
+    assert manufactured_grid_error() < 1e-10
+
+
+def test_hps_merge_solve_manufactured_rectangular_grid():
+    assert manufactured_grid_error(p=7, nx=2, ny=8, kappa=3.0, seed=5) < 1e-10
+
+
+def test_merge_schedule():
+    assert O.merge_schedule(8, 8) == ["x", "y"] * 3
+    assert O.merge_schedule(2, 8) == ["x", "y", "y", "y"]
+    assert O.merge_schedule(64, 128) == ["x", "y"] * 6 + ["y"]
+    with pytest.raises(ValueError):
+        O.merge_schedule(6, 8)
+
+
+def planewave_case(p, nx=8, ny=8):
+    w = WL.planewave(p=p, nx=nx, ny=ny)
+    coefs, fs = [], []
+    for box in w.boxes():
+        x, y = O.leaf_nodes(p, box)
+        coefs.append(w.coefficients(x, y))
+        fs.append(w.body_load(x, y))
+    return w, coefs, fs
+
+
+def test_hps_equals_global_dense_solve_planewave():
+    """Config: kappa = 20, b = 1, p = 10, 8 x 8 leaves (4096 interior + 896
+    interface unknowns); merge tree vs brute-force dense solve of the same
+    discrete system."""
+    p = 10
+    w, coefs, fs = planewave_case(p)
+    sol, _ = hps_grid_solve(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+    dense, res = O.global_dense_solve(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+    A, rhs, lay = O.global_system(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+    assert A.shape == (4992, 4992)
+    assert res < 1e-12
+    ref = [(d["u_b"], d["u_i"]) for d in dense]
+    assert grid_error(sol, ref) < 1e-10
+
+
+def test_planewave_spectral_convergence():
+    errs = []
+    for p in (6, 8, 10, 12, 14):
+        w, coefs, fs = planewave_case(p)
+        sol, _ = hps_grid_solve(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+        errs.append(grid_error(sol, nodal_values(p, 8, 8, w.dirichlet_data)))
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 10.0, errs
+    assert errs[-1] < 1e-8, errs
+
+
+def test_j0_spectral_convergence():
+    """The paper's closed-form test: u = J0(kappa |x - (-0.1, 0.5)|) solves the
+    homogeneous Helmholtz equation on [0,1]^2 (Section 3)."""
+    kappa = 20.0
+
+    def u_true(x, y):
+        return scipy.special.j0(kappa * np.hypot(x + 0.1, y - 0.5))
+
+    errs = []
+    for p in (8, 11, 14):
+        w, coefs, fs = planewave_case(p)
+        sol, _ = hps_grid_solve(p, 8, 8, coefs, kappa, fs, u_true)
+        errs.append(grid_error(sol, nodal_values(p, 8, 8, u_true)))
+    assert errs[1] < errs[0] / 30 and errs[2] < errs[1] / 30, errs
+    assert errs[-1] < 1e-8, errs
+
+
+def test_dtn_maps_planewave_trace_to_normal_derivative():
+    kappa, d = 20.0, (0.6, 0.8)
+    errs = []
+    for p in (8, 12, 16, 20):
+        box = (0.25, 0.5, 0.125, 0.125)
+        x, y = O.leaf_nodes(p, box)
+        coef = np.stack([np.ones(p * p), 0 * x, np.ones(p * p), 0 * x, 0 * x, np.ones(p * p)])
+        out = O.condense_leaf(p, box, coef, kappa)
+        ix = O.leaf_index_sets(p)
+        u = np.sin(kappa * (d[0] * x + d[1] * y))
+        ux = kappa * d[0] * np.cos(kappa * (d[0] * x + d[1] * y))
+        uy = kappa * d[1] * np.cos(kappa * (d[0] * x + d[1] * y))
+        dn = np.concatenate([-ux[ix["W"]], ux[ix["E"]], -uy[ix["S"]], uy[ix["N"]]])
+        errs.append(O.relerr(out["T"] @ u[ix["B"]], dn))
+        # S maps the trace to the interior values
+        assert O.relerr(out["S"] @ u[ix["B"]], u[ix["I"]]) < max(10 * errs[-1], 1e-12)
+    assert errs[-1] < 1e-9 and errs[1] < errs[0] / 100, errs
+
+
+# ----------------------------------------------------- planted-mistake checks
+
+def _leaf_pins():
+    rng = np.random.default_rng(3)
+    p, box, kappa = 8, (0.0, 0.0, 0.25, 0.125), 9.0
+    u = random_poly(rng, p - 1, p - 1, xc=0.125, yc=0.0625, sx=0.125, sy=0.0625)
+    coef = random_coef(rng, p * p)
+    e_op = operator_error(p, box, coef, kappa, u)
+    e_int, e_flux, _ = condense_errors(p, box, coef, kappa, u)
+    return max(e_op, e_int, e_flux), manufactured_grid_error(p=6, nx=2, ny=2, seed=4)
+
+
+def test_pins_pass_unmutated():
+    leaf, grid = _leaf_pins()
+    assert leaf < 1e-10 and grid < 1e-10
+
+
+@pytest.mark.parametrize("mutation", ["transpose_D", "flip_west_normal", "drop_c1",
+                                      "kappa_sign", "c12_factor", "swap_merge_order"])
+def test_planted_mistake_is_caught(monkeypatch, mutation):
+    real_diff, real_op, real_keys = O.cheb_diff, O.leaf_operator, O.box_keys
+    if mutation == "transpose_D":
+        monkeypatch.setattr(O, "cheb_diff", lambda p: real_diff(p).T)
+    elif mutation == "flip_west_normal":
+        def op(p, box, coef, kappa):
+            A, N, Dx, Dy = real_op(p, box, coef, kappa)
+            N = N.copy()
+            N[: p - 2] *= -1.0
+            return A, N, Dx, Dy
+        monkeypatch.setattr(O, "leaf_operator", op)
+    elif mutation == "drop_c1":
+        def op(p, box, coef, kappa):
+            c = np.array(coef, dtype=float)
+            A, N, Dx, Dy = real_op(p, box, c, kappa)
+            return A + c[3][:, None] * Dx, N, Dx, Dy
+        monkeypatch.setattr(O, "leaf_operator", op)
+    elif mutation == "kappa_sign":
+        def op(p, box, coef, kappa):
+            A, N, Dx, Dy = real_op(p, box, coef, kappa)
+            return A + 2 * kappa ** 2 * np.diag(np.asarray(coef[5], float)), N, Dx, Dy
+        monkeypatch.setattr(O, "leaf_operator", op)
+    elif mutation == "c12_factor":
+        def op(p, box, coef, kappa):
+            A, N, Dx, Dy = real_op(p, box, coef, kappa)
+            return A + np.asarray(coef[1], float)[:, None] * (Dx @ Dy), N, Dx, Dy
+        monkeypatch.setattr(O, "leaf_operator", op)
+    if mutation == "c12_factor":
+        rng = np.random.default_rng(8)
+        p, box = 8, (0.0, 0.0, 0.25, 0.125)
+        u = random_poly(rng, p - 1, p - 1, xc=0.125, yc=0.0625, sx=0.125, sy=0.0625)
+        err = operator_error(p, box, random_coef(rng, p * p, c12=True), 5.0, u)
+        assert err > 1e-6
+        return
+    if mutation == "swap_merge_order":
+        # leaf T is computed in [W, E, S, N] order; reversed leaf keys mislabel
+        # its rows, so the solve goes wrong or the key bookkeeping rejects it
+        def keys_bad(p, ix0, iy0, wx, wy):
+            k = real_keys(p, ix0, iy0, wx, wy)
+            return k[::-1] if (wx, wy) == (1, 1) else k
+        monkeypatch.setattr(O, "box_keys", keys_bad)
+        try:
+            err = manufactured_grid_error(p=6, nx=2, ny=2, seed=4)
+        except (AssertionError, KeyError):
+            return
+        assert err > 1e-6, err
+        return
+    leaf, grid = _leaf_pins()
+    assert max(leaf, grid) > 1e-6, (leaf, grid)
