@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of batched HPS leaf static condensation on one B300 per rank.
+
+Workload: the p = 20 unit-square problem (64 x 64 = 4096 leaves, A_ii of
+324 x 324, kappa = 200, b = 1 - 0.5 exp(-|x - (0.5, 0.5)|^2 / 0.02), one body
+load of 16 seeded Gaussian bumps), synthetic and resident in HBM.
+
+A step is one hps_condense call over all 4096 leaves (assembly, LU with
+partial pivoting, solves, DtN map): one kernel launch.  Two precision paths
+run on the same inputs: FP32 LU/solves with FP64 iterative refinement (the
+reported `value`) and plain FP64 (reported beside it).  The metric is leaf
+condensations per second; TFLOP/s use the algorithmic count per leaf
+(2/3 n_i^3 + 2 n_i^2 n_b + 2 n_b^2 (p-2)).
+
+Under torchrun every rank condenses its own copy of the workload (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "leaf condensations/s and TFLOP/s, mixed vs FP64 GPU path at rel err ≤1e-10"
+UNIT = "leaf condensations/s"
+
+
+def leaf_flops(p):
+    q = p - 2
+    n, nb = q * q, 4 * q
+    return (2.0 / 3.0) * n ** 3 + 2.0 * n * n * nb + 2.0 * nb * nb * q
+
+
+def peaks():
+    """Roofline denominators: FP32 and FP64 ALU peaks from unit counts and the
+    maximum SM clock (148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz); FP64 is
+    the nominal 1.25 TFLOP/s of the part.  HBM from the driver's measurement
+    when present."""
+    sm_mhz = 2032.0
+    hbm = None
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            mp = json.load(fh)
+        sm_mhz = mp.get("sm_max_mhz", sm_mhz)
+        hbm = mp.get("hbm_gbs")
+    fp32 = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return {"fp32_tflops": fp32, "fp64_tflops": 1.25, "hbm_gbs": hbm}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend=backend)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        mhz, mx, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            try:
+                mhz.append(float(parts[2]))
+                mx = float(parts[3])
+                power.append(float(parts[4]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- workload
+
+def make_inputs(w, plan):
+    """Coefficients and body loads at the library's node coordinates (host)."""
+    lay = plan.layout
+    xy = plan.leaf_nodes().cpu().numpy()
+    p2 = int(lay.p2[0])
+    X = xy.reshape(w.n_leaves, 2, p2)
+    x, y = X[:, 0, :], X[:, 1, :]
+    coef = np.ascontiguousarray(np.moveaxis(w.coefficients(x, y), 0, 1))  # (n, 6, p2)
+    f = np.ascontiguousarray(w.body_load(x, y))                            # (n, p2, m)
+    return coef.ravel(), f.ravel()
+
+
+def rel_leafwise(a, b, n_leaves):
+    a = a.reshape(n_leaves, -1)
+    b = b.reshape(n_leaves, -1)
+    num = (a - b).norm(dim=1)
+    den = b.norm(dim=1).clamp_min(1e-300)
+    return float((num / den).max())
+
+
+def time_steps(fn, steps, warmup, ws, stream, on_start=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if on_start is not None:
+        on_start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    return max_over_ranks(ms, ws)
+
+
+def cpu_baseline(w, budget_s, gpu_out=None, sample_cap=None):
+    """The FP64 oracle as it stands, leaf by leaf, on a bounded sample."""
+    import oracle.hps_oracle as O
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        cores = 1
+    boxes = w.boxes()
+    p = int(w.p[0])
+    rng = np.random.default_rng(1234)
+    order = rng.permutation(w.n_leaves)
+    done, t0 = [], time.perf_counter()
+    results = {}
+    for l in order:
+        x, y = O.leaf_nodes(p, boxes[l])
+        out = O.condense_leaf(p, boxes[l], w.coefficients(x, y), w.kappa, w.body_load(x, y).reshape(p * p, -1))
+        results[int(l)] = out
+        done.append(int(l))
+        if time.perf_counter() - t0 > budget_s or (sample_cap and len(done) >= sample_cap):
+            break
+    dt = time.perf_counter() - t0
+    rec = {"value": len(done) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(done)} random leaves of the 4096 (p=20), {dt:.1f} s, numpy/LAPACK FP64 "
+                     f"(OpenBLAS threads {cores})"}
+    return rec, results
+
+
+def parity_vs_oracle(w, lay, outs, results):
+    """Max per-leaf relative error of GPU outputs against the oracle leaves."""
+    worst = {}
+    for name, out in outs.items():
+        e = 0.0
+        for l, ref in results.items():
+            ni, nb = int(lay.ni[l]), int(lay.nb[l])
+            S = out["S"][int(lay.o_sb[l]):int(lay.o_sb[l + 1])].reshape(ni, nb)
+            T = out["T"][int(lay.o_bb[l]):int(lay.o_bb[l + 1])].reshape(nb, nb)
+            h = out["h"][int(lay.o_nb[l]):int(lay.o_nb[l + 1])].reshape(nb, 1)
+            W = out["W"][int(lay.o_ni[l]):int(lay.o_ni[l + 1])].reshape(ni, 1)
+            for a, b in ((S, ref["S"]), (T, ref["T"]), (h, ref["h"]), (W, ref["W"])):
+                e = max(e, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        worst[name] = e
+    return worst
+
+
+# ---------------------------------------------------------------- arms
+
+def config_block(w, ws):
+    return {"workload": "bumps_p20: unit square, 64x64 leaves (4096), p=20 (A_ii 324x324), kappa=200, "
+                        "b=1-0.5exp(-|x-c|^2/0.02), m=1 body load of 16 Gaussian bumps (seed 2)",
+            "n_leaves_per_rank": w.n_leaves, "p": 20, "m": w.m,
+            "parallelism": f"leaf-parallel, {ws} rank(s), no collective",
+            "l2": "no flush: per step the outputs alone are 0.95 GB (S 764 MB) > 126 MB L2"}
+
+
+def run_reference(args, rank, ws):
+    from paper_2211_14969_b300 import workloads as WL
+    if rank != 0:
+        return
+    w = WL.bumps_p20()
+    per_step = 16
+    # warmup
+    for _ in range(args.warmup):
+        cpu_baseline(w, 1e9, sample_cap=2)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        rec, _ = cpu_baseline(w, 1e9, sample_cap=per_step)
+        n += per_step
+    dt = time.perf_counter() - t0
+    value = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(w, 1),
+            "tflops": value * leaf_flops(20) / 1e12,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": rec["cores"], "kind": "oracle",
+                             "sample": f"{per_step} random leaves per step of the 4096 (p=20), FP64 numpy/LAPACK"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, ws):
+    import torch
+    from paper_2211_14969_b300 import hps
+    from paper_2211_14969_b300 import workloads as WL
+
+    w = WL.bumps_p20()
+    n = w.n_leaves
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    lay = plan.layout
+    coef_h, f_h = make_inputs(w, plan)
+    coef = torch.from_numpy(coef_h).cuda()
+    f = torch.from_numpy(f_h).cuda()
+    stream = torch.cuda.current_stream()
+    outs = {}
+    for name in ("fp32", "fp64"):
+        outs[name] = {"S": torch.empty(int(lay.o_sb[-1]), dtype=torch.float64, device="cuda"),
+                      "T": torch.empty(int(lay.o_bb[-1]), dtype=torch.float64, device="cuda"),
+                      "h": torch.empty(int(lay.o_nb[-1]), dtype=torch.float64, device="cuda"),
+                      "W": torch.empty(int(lay.o_ni[-1]), dtype=torch.float64, device="cuda"),
+                      "info": torch.empty(n, dtype=torch.int32, device="cuda")}
+    tol, kmax = 1e-12, 6
+
+    def step(name):
+        plan.condense(coef, f, m=1, prec=name, tol=tol, kmax=kmax, out=outs[name])
+
+    flops = n * leaf_flops(20)
+    pk = peaks()
+    res = {}
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    for name in ("fp64", "fp32"):
+        steps = args.steps
+        with ClockSampler(uuid) as cs:
+            ms = time_steps(lambda: step(name), steps, args.warmup, ws, stream,
+                            on_start=lambda: plan.set_timing(True))
+        kt = plan.phase_times()        # kernel-only events of the timed calls
+        plan.set_timing(False)
+        info = outs[name]["info"].cpu().numpy()
+        per_step = ms / steps
+        kernel_ms = kt[0] / kt[1]
+        peak = pk["fp64_tflops"] if name == "fp64" else pk["fp32_tflops"]
+        achieved = flops / (kernel_ms * 1e-3) / 1e12
+        res[name] = {"ms_per_step": per_step, "value": ws * n / (per_step * 1e-3),
+                     "tflops": ws * flops / (per_step * 1e-3) / 1e12, "kernel_ms": kernel_ms,
+                     "info_nonzero": int((info != 0).sum()),
+                     "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": achieved / peak, "traffic": None},
+                     "clocks": cs.summary()}
+    o64, o32 = outs["fp64"], outs["fp32"]
+    err = {k: rel_leafwise(o32[k], o64[k], n) for k in ("S", "T", "h", "W")}
+
+    # end to end through the C ABI with host buffers: H2D of the inputs,
+    # condensation, D2H of every output, each step
+    e2e = None
+    if rank == 0 or ws > 1:
+        coef_p = torch.from_numpy(coef_h).pin_memory()
+        f_p = torch.from_numpy(f_h).pin_memory()
+        host_out = {k: torch.empty(v.numel(), dtype=v.dtype).pin_memory() for k, v in o32.items()}
+
+        def e2e_step():
+            coef.copy_(coef_p, non_blocking=True)
+            f.copy_(f_p, non_blocking=True)
+            step("fp32")
+            for k, v in o32.items():
+                host_out[k].copy_(v, non_blocking=True)
+
+        ms_e2e = time_steps(e2e_step, max(2, args.steps // 2), 1, ws, stream)
+        steps_e2e = max(2, args.steps // 2)
+        h2d = coef_p.numel() * 8 + f_p.numel() * 8
+        d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+        e2e = {"value": ws * n / (ms_e2e / steps_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        parity = None
+        if ws == 1 and not args.no_cpu_baseline:
+            outs_np = {k: {kk: vv.cpu().numpy() for kk, vv in v.items()} for k, v in outs.items()}
+            cpu, results = cpu_baseline(w, args.cpu_seconds)
+            parity = parity_vs_oracle(w, lay, outs_np, results)
+        r32, r64 = res["fp32"], res["fp64"]
+        line = {"metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded Gaussian bumps, analytic coefficient field), resident in HBM",
+                "config": config_block(w, ws),
+                "tflops": r32["tflops"],
+                "precision_path": "fp32 LU/solves + fp64 residual refinement (tol 1e-12, kmax 6)",
+                "roofline": r32["roofline"],
+                "clocks": r32["clocks"],
+                "e2e": e2e,
+                "gpu_launches": args.steps,
+                "fp64_path": {"value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms_per_step"],
+                              "tflops": r64["tflops"], "dtype": "f64", "roofline": r64["roofline"],
+                              "clocks": r64["clocks"], "gpu_launches": args.steps},
+                "mixed_vs_fp64_max_leaf_relerr": err,
+                "info_nonzero": {"fp32": r32["info_nonzero"], "fp64": r64["info_nonzero"]},
+                "cpu_baseline": cpu,
+                "parity_vs_oracle_sampled": parity}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return line
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    rank, ws = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_gpu(args, rank, ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

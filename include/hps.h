@@ -1,0 +1,163 @@
+/*
+ * hps.h -- C ABI of libhps, batched HPS leaf static condensation on B300.
+ *
+ * Method: Yesypenko & Martinsson, "GPU Optimizations for the Hierarchical
+ * Poincare-Steklov Scheme" (arXiv 2211.14969).  The BVP is Eq. (bvp) with the
+ * variable-coefficient Helmholtz operator of Eq. (var_helm), written on a
+ * reference square in the general second-order form of Eq. (chain_rule):
+ *
+ *   A u = -(c11 u_xx + 2 c12 u_xy + c22 u_yy + c1 u_x + c2 u_y) - kappa^2 b u = f,
+ *
+ * discretized per Section 2: each leaf box carries a p x p tensor mesh of
+ * Chebyshev points, the PDE is collocated at the (p-2)^2 interior nodes, and
+ * the flux (outward normal derivative) is continuous across leaf edges.  The
+ * four leaf corners are not unknowns.  Static condensation (Section 2)
+ * eliminates the interior nodes of every leaf, leaving the reduced system of
+ * Eq. (hps_reduced) on the 4(p-2) edge nodes of each leaf.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Leaf box (x0, y0, hx, hy); node (i, j), i the x index, has id i*p + j
+ *    and coordinates x0 + (1 - cos(i pi/(p-1))) hx/2, y0 + (1 - cos(j pi/(p-1))) hy/2.
+ *  - Interior nodes (1 <= i, j <= p-2) in lexicographic order, i major:
+ *    n_i = (p-2)^2 of them.  Edge nodes in the order [W, E, S, N], each edge
+ *    by increasing coordinate: n_b = 4(p-2).
+ *  - Per-leaf arrays are packed leaf after leaf: leaf l starts at the sum of
+ *    the sizes of leaves 0..l-1 (for one p everywhere, l times the size).
+ *    Every matrix is row-major inside its leaf block.
+ *  - All pointers named d_* are device pointers on the current CUDA device,
+ *    owned by the caller, and must stay valid until the stream reaches the
+ *    work that reads or writes them.  Host pointers are read before the call
+ *    returns.  Every call is asynchronous on the given stream (NULL = legacy
+ *    default stream) and reports argument and launch errors synchronously.
+ *  - No call allocates or frees a caller buffer.  A plan owns its device
+ *    workspace (allocated at build time, grown on demand by hps_condense and
+ *    hps_merge, freed by hps_destroy).
+ *  - A plan is not thread-safe; use one plan per host thread or serialise.
+ */
+#ifndef HPS_H
+#define HPS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hps_plan hps_plan;
+typedef struct CUstream_st *hps_stream; /* a cudaStream_t */
+
+typedef enum {
+    HPS_OK = 0,
+    HPS_ERR_ARG = 1,      /* invalid argument; nothing was enqueued */
+    HPS_ERR_CUDA = 2,     /* a CUDA runtime call failed (message in hps_last_error) */
+    HPS_ERR_OOM = 3,      /* device workspace could not be allocated */
+    HPS_ERR_SINGULAR = 4, /* reserved for host-side checks of info[] */
+    HPS_ERR_NOCONV = 5,   /* reserved for host-side checks of info[] */
+    HPS_ERR_STATE = 6     /* call out of order (e.g. hps_solve before hps_merge) */
+} hps_status;
+
+typedef enum {
+    HPS_FP64 = 0,        /* everything in FP64 */
+    HPS_MIXED_FP32 = 1,  /* FP32 LU/TRSM, FP64 residual + iterative refinement */
+    HPS_MIXED_TF32 = 2,  /* reserved: TF32 tensor-core LU + FP64 refinement */
+    HPS_MIXED_BF16 = 3   /* reserved: BF16 tensor-core LU + FP64 refinement */
+} hps_prec;
+
+#define HPS_PMIN 4
+#define HPS_PMAX 42
+
+typedef struct {
+    int n_leaves;        /* >= 1 */
+    const int *p;        /* host [n_leaves]: points per direction, HPS_PMIN..HPS_PMAX */
+    const double *box;   /* host [n_leaves][4]: x0, y0, hx, hy (hx, hy > 0) */
+    double kappa;        /* wavenumber of Eq. (var_helm) */
+} hps_leaf_desc;
+
+/* Build a plan for a batch of leaves (Section 2: leaf boxes with p x p
+ * Chebyshev meshes).  Validates the description, forms the Chebyshev
+ * differentiation matrices of every order present in FP64, sorts the leaves
+ * into a longest-first work queue and allocates the per-CTA workspace.
+ * Returns HPS_ERR_ARG for a bad description (*out is set to NULL),
+ * HPS_ERR_OOM / HPS_ERR_CUDA on device failures. */
+hps_status hps_build_leaves(const hps_leaf_desc *desc, hps_plan **out, hps_stream stream);
+
+/* Node coordinates of every leaf, so the caller can sample coefficients:
+ * d_xy per leaf [2][p*p] (all x, then all y), packed.  Section 2 mesh. */
+hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream);
+
+/* Leaf static condensation (Section 2; steps: assemble the collocation
+ * operator, factor the interior block with partial pivoting, solve, form the
+ * DtN map).  For every leaf:
+ *   S = -A_ii^{-1} A_ib         (n_i x n_b)   solution operator
+ *   T = N_b + N_i S             (n_b x n_b)   Dirichlet-to-Neumann map
+ *   W = A_ii^{-1} f_I           (n_i x m)     particular interior solution
+ *   h = N_i W                   (n_b x m)     its outgoing flux
+ * where N = [N_b N_i] are the outward-normal-derivative rows at the edge nodes.
+ * Inputs:  d_coef per leaf [6][p*p]: c11, c12, c22, c1, c2, b at the nodes.
+ *          d_f per leaf [p*p][m] body loads at the nodes (interior used), or
+ *          NULL when m == 0.
+ * Outputs: d_S (may be NULL: not stored), d_T (required), d_W and d_h
+ *          (required when m > 0), d_info per leaf (required):
+ *            0     success,
+ *            k > 0 exact zero pivot at elimination step k (the leaf's S, T
+ *                  hold inf/NaN),
+ *            -k    mixed precision: refinement did not reach tol in k steps.
+ * prec: HPS_FP64 or HPS_MIXED_FP32 (others return HPS_ERR_ARG for now).
+ * tol, kmax: refinement stops when every correction is below tol relative
+ *            to the solution (max norm per column), after at most kmax
+ *            corrections; ignored for HPS_FP64.
+ * Corner rows: with c12 != 0 the interior rows touch the leaf corners, whose
+ * columns are dropped (corners are not unknowns). */
+hps_status hps_condense(hps_plan *plan, hps_prec prec, const double *d_coef, const double *d_f,
+                        int m, double tol, int kmax, double *d_S, double *d_T, double *d_h,
+                        double *d_W, int *d_info, hps_stream stream);
+
+/* Upward merges over a uniform-p nx x ny grid of leaves tiling a rectangle
+ * (leaf l = ix*ny + iy), nx and ny powers of two.  Each merge of boxes
+ * alpha, beta across their shared edge 3 (1, 2 their other edges) forms
+ *   Z = Ta33 + Tb33,  S3 = -Z^{-1}[Ta31 Tb32],  w3 = -Z^{-1}(ha3 + hb3),
+ *   T = diag(Ta11, Tb22) + [Ta13; Tb23] S3,  h = [ha1; hb2] + [Ta13; Tb23] w3,
+ * the Schur complement the paper takes from its HPS references (Section 2).
+ * Merges alternate x then y; box boundaries are ordered [W, E, S, N], each
+ * side by increasing coordinate.  d_T, d_h as written by hps_condense.  The
+ * plan stores S3, w3 of every merge; the root's T is not formed. */
+hps_status hps_merge(hps_plan *plan, int nx, int ny, const double *d_T, const double *d_h, int m,
+                     hps_stream stream);
+
+/* Top-down solve after hps_merge (Section 2 Remark: leaf values from the
+ * reduced solution).  d_g: Dirichlet data at the outer edge nodes in the
+ * root box order [W, E, S, N] (n_outer x m).  Shared-edge values come from
+ * u3 = S3 [u1; u2] + w3, leaf interiors from u_i = S u_b + W.
+ * d_u per leaf [p*p][m]: the solution at every node; the four corners are
+ * written as 0.  d_S and d_W as written by hps_condense (d_W may be NULL
+ * when the merge had m body loads of zero). */
+hps_status hps_solve(hps_plan *plan, const double *d_g, const double *d_S, const double *d_W,
+                     int m, double *d_u, hps_stream stream);
+
+/* Kernel timing with CUDA events recorded on the launch stream around the
+ * condensation kernel of every hps_condense call.  hps_set_timing(plan, 1)
+ * enables it and clears the record; hps_phase_times fills up to n values:
+ *   ms[0] total kernel time of the recorded calls (milliseconds),
+ *   ms[1] number of recorded calls,
+ *   ms[2] kernel time of the last recorded call.
+ * It waits for the recorded events.  HPS_ERR_STATE if timing is off or no
+ * call was recorded.  At most 4096 calls are recorded; later calls are not. */
+hps_status hps_set_timing(hps_plan *plan, int enable);
+hps_status hps_phase_times(hps_plan *plan, float *ms, int n);
+
+/* Number of kernel launches enqueued by the last hps_condense call. */
+int hps_last_launch_count(const hps_plan *plan);
+
+/* Last error message of this plan (or of the last failed build when plan
+ * is NULL); never NULL. */
+const char *hps_last_error(const hps_plan *plan);
+
+/* Free the plan and its workspace (synchronises the device first). */
+void hps_destroy(hps_plan *plan);
+
+/* ABI version: major * 100 + minor. */
+int hps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPS_H */

@@ -1,0 +1,547 @@
+// C ABI of libhps (declared in include/hps.h): plan construction, argument
+// checking, workspace management and the launch sequence of every call.
+// All numerical work runs in the kernels of condense.cu and merge.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hps.h"
+#include "hps_internal.cuh"
+#include "merge.cuh"
+
+using namespace hps;
+
+namespace {
+
+std::string g_build_error;  // message of the last failed hps_build_leaves
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t want) {
+        if (bytes >= want) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        else p = nullptr;
+        return e;
+    }
+};
+
+struct Level {
+    MergeLevelDev dev{};
+    DevBuf maps, aug, th, u, info;
+};
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+constexpr int kMaxTimed = 4096;
+
+// Chebyshev differentiation matrix on the p Chebyshev-Gauss-Lobatto points
+// of [-1, 1] in increasing order, from the barycentric weights
+// w_k = (-1)^k (1/2 at the ends): D_ij = (w_j / w_i) / (t_i - t_j), with the
+// node differences taken in the product form 2 sin(pi(i+j)/2N) sin(pi(i-j)/2N)
+// (Don & Solomonoff 1997) and the diagonal from the zero row sum.
+void chebyshev_matrix(int p, std::vector<double> &D) {
+    const int N = p - 1;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> w(p);
+    for (int k = 0; k < p; ++k) w[k] = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == N) ? 0.5 : 1.0);
+    D.assign((size_t)p * p, 0.0);
+    for (int i = 0; i < p; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < p; ++j) {
+            if (j == i) continue;
+            const double diff = 2.0 * std::sin(pi * (i + j) / (2.0 * N)) * std::sin(pi * (i - j) / (2.0 * N));
+            const double v = (w[j] / w[i]) / diff;
+            D[(size_t)i * p + j] = v;
+            s += v;
+        }
+        D[(size_t)i * p + i] = -s;
+    }
+}
+
+LuBlocking choose_blocking(size_t tsize, int nrows, size_t budget) {
+    LuBlocking b;
+    b.ch = 128;
+    b.ldp = nrows | 1;
+    b.nb_panel = 4;
+    for (int nb : {32, 16, 8, 4}) {
+        if ((size_t)nb * (b.ldp + b.ch) * tsize <= budget || nb == 4) {
+            b.nb_panel = nb;
+            break;
+        }
+    }
+    return b;
+}
+
+}  // namespace
+
+struct hps_plan {
+    int n_leaves = 0;
+    double kappa = 0.0;
+    std::vector<int> p;
+    std::vector<double> box;
+    int pmin = 0, pmax = 0;
+    bool uniform = true;
+    std::vector<long long> o_p2, o_ni, o_nb, o_sb, o_bb;
+    DevBuf tables, work;
+    int *d_p = nullptr, *d_order = nullptr, *d_doff = nullptr, *d_queue = nullptr;
+    double *d_box = nullptr, *d_dmat = nullptr;
+    long long *d_off = nullptr;  // o_p2, o_ni, o_nb, o_sb, o_bb back to back
+    int device = 0, sms = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // pairs around each recorded kernel
+    int n_timed = 0;
+    int launches = 0;
+    // merge tree
+    std::vector<Level> levels;
+    DevBuf u_leaf;
+    int merge_nx = 0, merge_ny = 0, merge_m = -1;
+    bool merged = false;
+    std::string err;
+
+    hps_status fail(hps_status s, const std::string &msg) {
+        err = msg;
+        return s;
+    }
+    hps_status cuda_fail(cudaError_t e, const char *where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? HPS_ERR_OOM : HPS_ERR_CUDA;
+    }
+    // event pair i (created on first use)
+    cudaEvent_t *event_pair(int i) {
+        while ((int)ev.size() < 2 * (i + 1)) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev.push_back(e);
+        }
+        return &ev[2 * i];
+    }
+    LeafTables leaf_tables() const {
+        LeafTables t;
+        t.p = d_p;
+        t.box = d_box;
+        const long long nl = n_leaves;
+        t.o_p2 = d_off;
+        t.o_ni = d_off + nl;
+        t.o_nb = d_off + 2 * nl;
+        t.o_sb = d_off + 3 * nl;
+        t.o_bb = d_off + 4 * nl;
+        t.order = d_order;
+        return t;
+    }
+};
+
+extern "C" {
+
+int hps_version(void) { return 100; }
+
+const char *hps_last_error(const hps_plan *plan) {
+    if (plan == nullptr) return g_build_error.c_str();
+    return plan->err.c_str();
+}
+
+hps_status hps_build_leaves(const hps_leaf_desc *desc, hps_plan **out, hps_stream stream) {
+    if (out == nullptr) {
+        g_build_error = "hps_build_leaves: out is NULL";
+        return HPS_ERR_ARG;
+    }
+    *out = nullptr;
+    if (desc == nullptr || desc->n_leaves < 1 || desc->p == nullptr || desc->box == nullptr) {
+        g_build_error = "hps_build_leaves: empty or NULL leaf description";
+        return HPS_ERR_ARG;
+    }
+    if (!std::isfinite(desc->kappa)) {
+        g_build_error = "hps_build_leaves: kappa is not finite";
+        return HPS_ERR_ARG;
+    }
+    const int nl = desc->n_leaves;
+    for (int l = 0; l < nl; ++l) {
+        const int p = desc->p[l];
+        const double *b = desc->box + 4LL * l;
+        if (p < HPS_PMIN || p > HPS_PMAX) {
+            g_build_error = "hps_build_leaves: leaf " + std::to_string(l) + " has p = " + std::to_string(p) +
+                            " outside [" + std::to_string(HPS_PMIN) + ", " + std::to_string(HPS_PMAX) + "]";
+            return HPS_ERR_ARG;
+        }
+        if (!(b[2] > 0.0) || !(b[3] > 0.0) || !std::isfinite(b[0]) || !std::isfinite(b[1]) ||
+            !std::isfinite(b[2]) || !std::isfinite(b[3])) {
+            g_build_error = "hps_build_leaves: leaf " + std::to_string(l) + " has an invalid box";
+            return HPS_ERR_ARG;
+        }
+    }
+    hps_plan *P = new hps_plan();
+    P->n_leaves = nl;
+    P->kappa = desc->kappa;
+    P->p.assign(desc->p, desc->p + nl);
+    P->box.assign(desc->box, desc->box + 4LL * nl);
+    P->pmin = *std::min_element(P->p.begin(), P->p.end());
+    P->pmax = *std::max_element(P->p.begin(), P->p.end());
+    P->uniform = P->pmin == P->pmax;
+    P->o_p2.resize(nl); P->o_ni.resize(nl); P->o_nb.resize(nl); P->o_sb.resize(nl); P->o_bb.resize(nl);
+    long long a = 0, b = 0, c = 0, d = 0, e = 0;
+    for (int l = 0; l < nl; ++l) {
+        const long long p = P->p[l], q = p - 2;
+        P->o_p2[l] = a; P->o_ni[l] = b; P->o_nb[l] = c; P->o_sb[l] = d; P->o_bb[l] = e;
+        a += p * p; b += q * q; c += 4 * q; d += q * q * 4 * q; e += 16 * q * q;
+    }
+    // largest leaves first; equal orders keep their index order
+    std::vector<int> order(nl);
+    for (int l = 0; l < nl; ++l) order[l] = l;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return P->p[x] > P->p[y]; });
+    // Chebyshev tables for every order present
+    std::vector<int> doff(HPS_PMAX + 1, -1);
+    std::vector<double> dmat;
+    for (int p = HPS_PMIN; p <= HPS_PMAX; ++p) {
+        if (std::find(P->p.begin(), P->p.end(), p) == P->p.end()) continue;
+        std::vector<double> D;
+        chebyshev_matrix(p, D);
+        doff[p] = (int)dmat.size();
+        dmat.insert(dmat.end(), D.begin(), D.end());
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < p; ++k) s += D[(size_t)i * p + k] * D[(size_t)k * p + j];
+                dmat.push_back(s);
+            }
+    }
+    cudaError_t err = cudaGetDevice(&P->device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (err != cudaSuccess) {
+        g_build_error = std::string("hps_build_leaves: ") + cudaGetErrorString(err);
+        delete P;
+        return HPS_ERR_CUDA;
+    }
+    // one allocation for all tables
+    const size_t sz_p = round_up(sizeof(int) * nl, 256), sz_box = round_up(sizeof(double) * 4 * nl, 256);
+    const size_t sz_off = round_up(sizeof(long long) * 5 * nl, 256), sz_ord = sz_p;
+    const size_t sz_doff = round_up(sizeof(int) * (HPS_PMAX + 1), 256);
+    const size_t sz_dmat = round_up(sizeof(double) * std::max<size_t>(dmat.size(), 1), 256);
+    const size_t sz_q = 256;
+    err = P->tables.ensure(sz_p + sz_box + sz_off + sz_ord + sz_doff + sz_dmat + sz_q);
+    if (err != cudaSuccess) {
+        g_build_error = std::string("hps_build_leaves: cudaMalloc: ") + cudaGetErrorString(err);
+        delete P;
+        return err == cudaErrorMemoryAllocation ? HPS_ERR_OOM : HPS_ERR_CUDA;
+    }
+    unsigned char *base = (unsigned char *)P->tables.p;
+    P->d_p = (int *)base; base += sz_p;
+    P->d_box = (double *)base; base += sz_box;
+    P->d_off = (long long *)base; base += sz_off;
+    P->d_order = (int *)base; base += sz_ord;
+    P->d_doff = (int *)base; base += sz_doff;
+    P->d_dmat = (double *)base; base += sz_dmat;
+    P->d_queue = (int *)base;
+    std::vector<long long> off;
+    off.reserve(5LL * nl);
+    for (auto *v : {&P->o_p2, &P->o_ni, &P->o_nb, &P->o_sb, &P->o_bb}) off.insert(off.end(), v->begin(), v->end());
+    cudaStream_t s = (cudaStream_t)stream;
+    err = cudaMemcpyAsync(P->d_p, P->p.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(P->d_box, P->box.data(), sizeof(double) * 4 * nl, cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(P->d_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(P->d_order, order.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(P->d_doff, doff.data(), sizeof(int) * doff.size(), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess && !dmat.empty())
+        err = cudaMemcpyAsync(P->d_dmat, dmat.data(), sizeof(double) * dmat.size(), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);  // host staging vectors die here
+    if (err != cudaSuccess) {
+        g_build_error = std::string("hps_build_leaves: upload: ") + cudaGetErrorString(err);
+        delete P;
+        return HPS_ERR_CUDA;
+    }
+    *out = P;
+    return HPS_OK;
+}
+
+hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream) {
+    if (plan == nullptr || d_xy == nullptr) return HPS_ERR_ARG;
+    cudaError_t e = launch_leaf_nodes(plan->leaf_tables(), plan->n_leaves, d_xy, (cudaStream_t)stream);
+    if (e != cudaSuccess) return const_cast<hps_plan *>(plan)->cuda_fail(e, "hps_leaf_nodes");
+    return HPS_OK;
+}
+
+hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const double *d_f, int m,
+                        double tol, int kmax, double *d_S, double *d_T, double *d_h, double *d_W,
+                        int *d_info, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (prec != HPS_FP64 && prec != HPS_MIXED_FP32)
+        return P->fail(HPS_ERR_ARG, "hps_condense: precision not supported (use HPS_FP64 or HPS_MIXED_FP32)");
+    if (d_coef == nullptr || d_T == nullptr || d_info == nullptr)
+        return P->fail(HPS_ERR_ARG, "hps_condense: d_coef, d_T and d_info are required");
+    if (m < 0) return P->fail(HPS_ERR_ARG, "hps_condense: m < 0");
+    if (m > 0 && (d_f == nullptr || d_h == nullptr))
+        return P->fail(HPS_ERR_ARG, "hps_condense: m > 0 needs d_f and d_h");
+    if (prec != HPS_FP64 && (kmax < 0 || !(tol >= 0.0)))
+        return P->fail(HPS_ERR_ARG, "hps_condense: kmax < 0 or tol < 0");
+    const bool mixed = prec != HPS_FP64;
+    const size_t tsize = mixed ? sizeof(float) : sizeof(double);
+    const int qmax = P->pmax - 2, nmax = qmax * qmax;
+    const LuBlocking blk = choose_blocking(tsize, nmax, 72 * 1024);
+    const size_t smem = lu_smem_bytes(blk, tsize);
+    const int per_sm = condense_max_ctas_per_sm(prec, smem);
+    if (per_sm < 1) return P->fail(HPS_ERR_CUDA, "hps_condense: kernel does not fit on an SM");
+    const int grid = std::min(P->n_leaves, P->sms * per_sm);
+    long long slot = 0;
+    for (int p = P->pmin; p <= P->pmax; ++p) {
+        const long long q = p - 2, n = q * q, r = 4 * q + m, C = n + r, LDC = round_up(C, 4);
+        long long b = n * LDC * (long long)tsize;
+        if (mixed) b = round_up(b, 256) + n * r * 8 + n * 4;
+        slot = std::max(slot, round_up(b, 256));
+    }
+    cudaError_t e = P->work.ensure((size_t)slot * grid);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense: workspace");
+    CondenseParams prm{};
+    prm.blk = blk;
+    prm.lt = P->leaf_tables();
+    prm.dt.dmat = P->d_dmat;
+    prm.dt.doff = P->d_doff;
+    prm.n_leaves = P->n_leaves;
+    prm.m = m;
+    prm.kappa2 = P->kappa * P->kappa;
+    prm.coef = d_coef;
+    prm.f = m > 0 ? d_f : nullptr;
+    prm.S = d_S;
+    prm.T = d_T;
+    prm.h = m > 0 ? d_h : nullptr;
+    prm.W = m > 0 ? d_W : nullptr;
+    prm.info = d_info;
+    prm.work = (unsigned char *)P->work.p;
+    prm.slot_bytes = slot;
+    prm.queue = P->d_queue;
+    prm.tol = tol;
+    prm.kmax = kmax;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(P->d_queue, 0, sizeof(int), s);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense: queue reset");
+    cudaEvent_t *evp = nullptr;
+    if (P->timing && P->n_timed < kMaxTimed) {
+        evp = P->event_pair(P->n_timed);
+        if (evp == nullptr) return P->fail(HPS_ERR_CUDA, "hps_condense: cudaEventCreate failed");
+        cudaEventRecord(evp[0], s);
+    }
+    e = mixed ? launch_condense_mixed32(prm, grid, smem, s) : launch_condense_fp64(prm, grid, smem, s);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense: launch");
+    if (evp) {
+        cudaEventRecord(evp[1], s);
+        ++P->n_timed;
+    }
+    P->launches = 1;
+    return HPS_OK;
+}
+
+hps_status hps_set_timing(hps_plan *P, int enable) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    P->timing = enable != 0;
+    P->n_timed = 0;
+    return HPS_OK;
+}
+
+hps_status hps_phase_times(hps_plan *P, float *ms, int n) {
+    if (P == nullptr || ms == nullptr || n < 1) return HPS_ERR_ARG;
+    if (!P->timing || P->n_timed == 0)
+        return P->fail(HPS_ERR_STATE, "hps_phase_times: timing not enabled or no call recorded");
+    double total = 0.0;
+    float last = 0.0f;
+    for (int i = 0; i < P->n_timed; ++i) {
+        cudaError_t e = cudaEventSynchronize(P->ev[2 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&last, P->ev[2 * i], P->ev[2 * i + 1]);
+        if (e != cudaSuccess) return P->cuda_fail(e, "hps_phase_times");
+        total += last;
+    }
+    const float vals[3] = {(float)total, (float)P->n_timed, last};
+    for (int i = 0; i < n; ++i) ms[i] = i < 3 ? vals[i] : 0.0f;
+    return HPS_OK;
+}
+
+int hps_last_launch_count(const hps_plan *P) { return P ? P->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Merge tree
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct HostLevel {
+    int dir;  // 0: x, 1: y
+    int wx, wy;   // child box size in leaves
+    int nm, n3, np, nbc;
+    std::vector<int> ca, cb, par_child, par_idx, s3a, s3b, srca, srcb;
+};
+
+// Boundary of a box of wx x wy leaves: [W (wy q), E (wy q), S (wx q), N (wx q)].
+void build_level(int q, int dir, int wx, int wy, int nbx, int nby, HostLevel &H) {
+    H.dir = dir;
+    H.wx = wx;
+    H.wy = wy;
+    const int Wc = 0, Ec = wy * q, Sc = 2 * wy * q, Nc = 2 * wy * q + wx * q;
+    H.nbc = 2 * (wx + wy) * q;
+    if (dir == 0) {
+        H.n3 = wy * q;
+        H.np = 2 * (2 * wx + wy) * q;
+        auto add = [&](int ch, int idx) { H.par_child.push_back(ch); H.par_idx.push_back(idx); };
+        for (int k = 0; k < wy * q; ++k) add(0, Wc + k);          // W' = alpha.W
+        for (int k = 0; k < wy * q; ++k) add(1, Ec + k);          // E' = beta.E
+        for (int k = 0; k < wx * q; ++k) add(0, Sc + k);          // S' = alpha.S, beta.S
+        for (int k = 0; k < wx * q; ++k) add(1, Sc + k);
+        for (int k = 0; k < wx * q; ++k) add(0, Nc + k);          // N' = alpha.N, beta.N
+        for (int k = 0; k < wx * q; ++k) add(1, Nc + k);
+        for (int k = 0; k < H.n3; ++k) { H.s3a.push_back(Ec + k); H.s3b.push_back(Wc + k); }
+        H.nm = (nbx / 2) * nby;
+        for (int px = 0; px < nbx / 2; ++px)
+            for (int py = 0; py < nby; ++py) {
+                H.ca.push_back((2 * px) * nby + py);
+                H.cb.push_back((2 * px + 1) * nby + py);
+            }
+    } else {
+        H.n3 = wx * q;
+        H.np = 2 * (wx + 2 * wy) * q;
+        auto add = [&](int ch, int idx) { H.par_child.push_back(ch); H.par_idx.push_back(idx); };
+        for (int k = 0; k < wy * q; ++k) add(0, Wc + k);          // W' = alpha.W, beta.W
+        for (int k = 0; k < wy * q; ++k) add(1, Wc + k);
+        for (int k = 0; k < wy * q; ++k) add(0, Ec + k);          // E' = alpha.E, beta.E
+        for (int k = 0; k < wy * q; ++k) add(1, Ec + k);
+        for (int k = 0; k < wx * q; ++k) add(0, Sc + k);          // S' = alpha.S
+        for (int k = 0; k < wx * q; ++k) add(1, Nc + k);          // N' = beta.N
+        for (int k = 0; k < H.n3; ++k) { H.s3a.push_back(Nc + k); H.s3b.push_back(Sc + k); }
+        H.nm = nbx * (nby / 2);
+        for (int px = 0; px < nbx; ++px)
+            for (int py = 0; py < nby / 2; ++py) {
+                H.ca.push_back(px * nby + 2 * py);
+                H.cb.push_back(px * nby + 2 * py + 1);
+            }
+    }
+    H.srca.assign(H.nbc, 0);
+    H.srcb.assign(H.nbc, 0);
+    for (int k = 0; k < H.n3; ++k) {
+        H.srca[H.s3a[k]] = -(k + 1);
+        H.srcb[H.s3b[k]] = -(k + 1);
+    }
+    for (int P = 0; P < H.np; ++P) (H.par_child[P] == 0 ? H.srca : H.srcb)[H.par_idx[P]] = P;
+}
+
+bool pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const double *d_h, int m,
+                     hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (!P->uniform) return P->fail(HPS_ERR_ARG, "hps_merge: needs one p on every leaf");
+    if (!pow2(nx) || !pow2(ny) || (long long)nx * ny != P->n_leaves)
+        return P->fail(HPS_ERR_ARG, "hps_merge: nx, ny must be powers of two with nx*ny = n_leaves");
+    if (d_T == nullptr || m < 0 || (m > 0 && d_h == nullptr))
+        return P->fail(HPS_ERR_ARG, "hps_merge: d_T required, d_h required when m > 0");
+    const int q = P->pmin - 2;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto &L : P->levels) {
+        L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
+    }
+    P->levels.clear();
+    P->merged = false;
+    int wx = 1, wy = 1;
+    std::vector<HostLevel> hl;
+    while (wx < nx || wy < ny) {
+        const int dir = (wx < nx && (wx <= wy || wy == ny)) ? 0 : 1;
+        HostLevel H;
+        build_level(q, dir, wx, wy, nx / wx, ny / wy, H);
+        hl.push_back(H);
+        if (dir == 0) wx *= 2; else wy *= 2;
+    }
+    P->levels.resize(hl.size());
+    cudaError_t e = cudaSuccess;
+    for (size_t li = 0; li < hl.size(); ++li) {
+        const HostLevel &H = hl[li];
+        Level &L = P->levels[li];
+        std::vector<int> maps;
+        auto put = [&](const std::vector<int> &v) { size_t o = maps.size(); maps.insert(maps.end(), v.begin(), v.end()); return o; };
+        const size_t oca = put(H.ca), ocb = put(H.cb), opc = put(H.par_child), opi = put(H.par_idx);
+        const size_t o3a = put(H.s3a), o3b = put(H.s3b), osa = put(H.srca), osb = put(H.srcb);
+        const bool root = li + 1 == hl.size();
+        const int lda = (int)round_up(H.n3 + H.np + m, 4);
+        if ((e = L.maps.ensure(maps.size() * sizeof(int))) != cudaSuccess) break;
+        if ((e = L.aug.ensure((size_t)H.nm * H.n3 * lda * sizeof(double))) != cudaSuccess) break;
+        if (!root && (e = L.th.ensure((size_t)H.nm * H.np * (H.np + m) * sizeof(double))) != cudaSuccess) break;
+        if ((e = L.u.ensure((size_t)H.nm * H.np * std::max(m, 1) * sizeof(double))) != cudaSuccess) break;
+        if ((e = L.info.ensure((size_t)H.nm * sizeof(int))) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(L.maps.p, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        const int *mp = (const int *)L.maps.p;
+        MergeLevelDev &D = L.dev;
+        D.nm = H.nm; D.n3 = H.n3; D.np = H.np; D.nbc = H.nbc; D.m = m; D.lda = lda;
+        D.ca = mp + oca; D.cb = mp + ocb; D.par_child = mp + opc; D.par_idx = mp + opi;
+        D.s3a = mp + o3a; D.s3b = mp + o3b; D.srca = mp + osa; D.srcb = mp + osb;
+        D.leaf_T = li == 0 ? d_T : nullptr;
+        D.leaf_h = li == 0 ? (m > 0 ? d_h : nullptr) : nullptr;
+        D.prev_Th = li == 0 ? nullptr : (const double *)P->levels[li - 1].th.p;
+        D.aug = (double *)L.aug.p;
+        D.Th = root ? nullptr : (double *)L.th.p;
+        D.info = (int *)L.info.p;
+        const LuBlocking blk = choose_blocking(sizeof(double), H.n3, 100 * 1024);
+        if ((e = launch_merge_level(D, !root, blk, s)) != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_merge");
+    if ((e = P->u_leaf.ensure((size_t)P->n_leaves * 4 * q * std::max(m, 1) * sizeof(double))) != cudaSuccess)
+        return P->cuda_fail(e, "hps_merge: leaf boundary buffer");
+    P->merge_nx = nx;
+    P->merge_ny = ny;
+    P->merge_m = m;
+    P->merged = true;
+    P->launches = 0;
+    for (auto &L : P->levels) P->launches += (L.dev.Th ? 3 : 2);
+    return HPS_OK;
+}
+
+hps_status hps_solve(hps_plan *P, const double *d_g, const double *d_S, const double *d_W, int m,
+                     double *d_u, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (!P->merged) return P->fail(HPS_ERR_STATE, "hps_solve: call hps_merge first");
+    if (m < 1 || m != P->merge_m)
+        return P->fail(HPS_ERR_ARG, "hps_solve: m must equal the m of hps_merge and be >= 1");
+    if (d_g == nullptr || d_S == nullptr || d_u == nullptr)
+        return P->fail(HPS_ERR_ARG, "hps_solve: d_g, d_S and d_u are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int p = P->pmin;
+    cudaError_t e = cudaSuccess;
+    const double *ub = d_g;
+    const int nl = (int)P->levels.size();
+    for (int li = nl - 1; li >= 0; --li) {
+        const Level &L = P->levels[li];
+        // parents of level li are the children of level li + 1, whose values
+        // the previous iteration wrote into L.u; the root takes the data g
+        const double *upar = (li == nl - 1) ? d_g : (const double *)L.u.p;
+        double *uch = li > 0 ? (double *)P->levels[li - 1].u.p : (double *)P->u_leaf.p;
+        if ((e = launch_merge_down(L.dev, upar, uch, s)) != cudaSuccess) break;
+        ub = uch;
+    }
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_solve: downward pass");
+    e = launch_leaf_recover(P->n_leaves, p, m, d_S, d_W, ub, d_u, s);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_solve: leaf recovery");
+    P->launches = nl + 1;
+    return HPS_OK;
+}
+
+void hps_destroy(hps_plan *P) {
+    if (P == nullptr) return;
+    cudaDeviceSynchronize();
+    for (auto &L : P->levels) {
+        L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
+    }
+    P->u_leaf.release();
+    P->work.release();
+    P->tables.release();
+    for (cudaEvent_t ev : P->ev) cudaEventDestroy(ev);
+    delete P;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+"""GPU parity of the full HPS pipeline (condense + merge + solve) on uniform
+leaf grids against the CPU oracle's merge tree, the brute-force dense global
+collocation solve, closed-form solutions and manufactured polynomials."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.hps_oracle as O
+from gpu_cases import gpu_inputs
+from manufactured import random_coef, random_poly
+from paper_2211_14969_b300 import hps
+from paper_2211_14969_b300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_pipeline(w, prec="fp64", coef_fn=None, load_fn=None, g_fn=None):
+    p = int(w.p[0])
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan, coef_fn, load_fn)
+    out = plan.condense(coef, f, m=1, prec=prec, tol=1e-13, kmax=8)
+    plan.merge(w.nx, w.ny, out["T"], out["h"], 1)
+    keys = O.outer_boundary_keys(p, w.nx, w.ny)
+    # Dirichlet data at the outer edge nodes, [W, E, S, N] of the root box
+    g = np.array([(g_fn or w.dirichlet_data)(*O.key_coords(p, k, w.nx, w.ny)) for k in keys], dtype=np.float64)
+    u = plan.solve(torch.from_numpy(g).cuda(), out["S"], out["W"], 1)
+    torch.cuda.synchronize()
+    assert (out["info"].cpu().numpy() == 0).all()
+    return u.cpu().numpy().reshape(w.n_leaves, p * p)
+
+
+def oracle_pipeline(w, coef_fn=None, load_fn=None, g_fn=None):
+    p = int(w.p[0])
+    boxes = w.boxes()
+    coefs, fs = [], []
+    for box in boxes:
+        x, y = O.leaf_nodes(p, box)
+        coefs.append((coef_fn or w.coefficients)(x, y))
+        fs.append((load_fn or w.body_load)(x, y).reshape(p * p, 1))
+    leaves = [O.condense_leaf(p, boxes[l], coefs[l], w.kappa, fs[l]) for l in range(w.n_leaves)]
+    levels = O.hps_upward(p, w.nx, w.ny, leaves)
+    gk = {k: np.atleast_1d((g_fn or w.dirichlet_data)(*O.key_coords(p, k, w.nx, w.ny)))
+          for k in O.outer_boundary_keys(p, w.nx, w.ny)}
+    sol = O.hps_downward(p, w.nx, w.ny, levels, leaves, gk)
+    return sol, coefs, fs
+
+
+def grid_from_sol(sol, p):
+    ix = O.leaf_index_sets(p)
+    out = np.zeros((len(sol), p * p))
+    for l, s in enumerate(sol):
+        out[l, ix["B"]] = s["u_b"].ravel()
+        out[l, ix["I"]] = s["u_i"].ravel()
+    return out
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_planewave_pipeline_matches_oracle_dense_and_closed_form():
+    """kappa = 20, b = 1, p = 10, 8 x 8 leaves, Dirichlet data of the plane
+    wave sin(kappa (0.6 x + 0.8 y)): condense, merge, solve on the GPU."""
+    w = WL.planewave()
+    p = 10
+    u_gpu = gpu_pipeline(w)
+    sol, coefs, fs = oracle_pipeline(w)
+    u_ora = grid_from_sol(sol, p)
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    assert rel(u_gpu[:, mask], u_ora[:, mask]) < 1e-12
+    dense, res = O.global_dense_solve(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+    assert rel(u_gpu[:, mask], grid_from_sol(dense, p)[:, mask]) < 1e-11
+    exact = np.stack([w.dirichlet_data(*O.leaf_nodes(p, b)) for b in w.boxes()])
+    err = rel(u_gpu[:, mask], exact[:, mask])
+    assert err < 1e-4, err
+    assert np.all(u_gpu[:, ~mask] == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_manufactured_polynomial_is_exact(prec):
+    """A tensor polynomial of degree p-1 is the exact discrete solution for
+    any coefficient samples: the GPU pipeline reproduces it to rounding."""
+    p, nx, ny, kappa = 8, 4, 4, 7.0
+    rng = np.random.default_rng(11)
+    u = random_poly(rng, p - 1, p - 1, xc=0.5, yc=0.5, sx=0.5, sy=0.5)
+    w = WL.bumps(p=p, nx=nx, ny=ny, kappa=kappa, seed=1, m=1)
+    coef_cache = {}
+
+    def coef_fn(x, y):
+        key = (round(float(x.min()), 12), round(float(y.min()), 12))
+        if key not in coef_cache:
+            r = np.random.default_rng(abs(hash(key)) % (2 ** 32))
+            coef_cache[key] = random_coef(r, x.size)
+        return coef_cache[key]
+
+    def load_fn(x, y):
+        return u.apply_operator(x, y, coef_fn(x, y), kappa)[:, None]
+
+    u_gpu = gpu_pipeline(w, prec, coef_fn, load_fn, lambda x, y: u(x, y))
+    exact = np.stack([u(*O.leaf_nodes(p, b)) for b in w.boxes()])
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    assert rel(u_gpu[:, mask], exact[:, mask]) < 1e-10
+
+
+def test_rectangular_grid_and_body_load():
+    """2 x 8 leaves (x merge once, then y only), variable b and bumps."""
+    w = WL.bumps(p=9, nx=2, ny=8, kappa=15.0, seed=4, m=1)
+    w.dirichlet = "planewave"
+    p = 9
+    u_gpu = gpu_pipeline(w)
+    sol, _, _ = oracle_pipeline(w)
+    u_ora = grid_from_sol(sol, p)
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    assert rel(u_gpu[:, mask], u_ora[:, mask]) < 1e-12
+
+
+def test_single_leaf_solve():
+    w = WL.planewave(p=12, nx=1, ny=1, kappa=6.0)
+    u_gpu = gpu_pipeline(w)
+    sol, _, _ = oracle_pipeline(w)
+    mask = np.ones(144, bool)
+    mask[[0, 11, 132, 143]] = False
+    assert rel(u_gpu[:, mask], grid_from_sol(sol, 12)[:, mask]) < 1e-12
+
+
+def test_merge_argument_errors():
+    w = WL.planewave(p=6, nx=2, ny=2)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    T = torch.zeros(int(plan.layout.o_bb[-1]), dtype=torch.float64, device="cuda")
+    with pytest.raises(hps.HpsError):
+        plan.merge(3, 2, T, None, 0)          # not powers of two / wrong count
+    with pytest.raises(hps.HpsError):
+        g = torch.zeros(16, dtype=torch.float64, device="cuda")
+        S = torch.zeros(int(plan.layout.o_sb[-1]), dtype=torch.float64, device="cuda")
+        plan.solve(g, S, None, 1)             # solve before merge
