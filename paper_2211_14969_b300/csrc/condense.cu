@@ -39,21 +39,24 @@ __device__ __forceinline__ void edge_node(int t, int q, int &k, int &l) {
 }
 
 struct LeafInfo {
-    int p, q, n, nbd, m, r, C, LDC;
+    int p, q, n, n4, nbd, m, r, C, LDC;
     double sx, sy;
     const double *D, *D2, *coef, *f;
     int flags;  // bit 0: c12 != 0, bit 1: c1 != 0, bit 2: c2 != 0
 };
 
+// Workspace layout of one leaf: M = [A_ii | zero pad to n4 | -A_ib | f_I],
+// row-major, ld LDC (a multiple of 4).
 __device__ LeafInfo leaf_info(const CondenseParams &P, int leaf) {
     LeafInfo L;
     L.p = P.lt.p[leaf];
     L.q = L.p - 2;
     L.n = L.q * L.q;
+    L.n4 = (L.n + 3) & ~3;
     L.nbd = 4 * L.q;
     L.m = P.m;
     L.r = L.nbd + L.m;
-    L.C = L.n + L.r;
+    L.C = L.n4 + L.r;
     L.LDC = (L.C + 3) & ~3;
     const double *box = P.lt.box + 4 * (long long)leaf;
     L.sx = 2.0 / box[2];
@@ -96,11 +99,14 @@ __device__ __forceinline__ double op_entry(const LeafInfo &L, int i, int j, int 
     return v;
 }
 
-// M (row-major, ld LDC) <- [A_ii | -A_ib | f_I].
+// M (row-major, ld LDC) <- [A_ii | 0 | -A_ib | f_I].  Entries that are
+// structurally zero (no shared grid line, c12 == 0) are written without
+// any FP64 arithmetic.
 template <typename T>
 __device__ void assemble(T *__restrict__ M, const LeafInfo &L, double kappa2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p = L.p, q = L.q, p2 = p * p, nA = L.n + L.nbd;
+    const int p = L.p, q = L.q, p2 = p * p, nA = L.n4 + L.nbd;
+    const bool dense = (L.flags & 1) != 0;
     for (int rr = warp; rr < L.n; rr += NWARP) {
         const int i = rr / q + 1, j = rr % q + 1, node = i * p + j;
         const double c11 = L.coef[node], c12 = L.coef[p2 + node], c22 = L.coef[2 * p2 + node];
@@ -108,17 +114,19 @@ __device__ void assemble(T *__restrict__ M, const LeafInfo &L, double kappa2) {
         const double b = L.coef[5 * p2 + node];
         T *row = M + (long long)rr * L.LDC;
         for (int c = lane; c < L.C; c += 32) {
-            double v;
-            if (c < nA) {
+            T val = T(0);
+            if (c < L.n || (c >= L.n4 && c < nA)) {
                 int k, l;
                 if (c < L.n) { k = c / q + 1; l = c % q + 1; }
-                else edge_node(c - L.n, q, k, l);
-                v = op_entry(L, i, j, k, l, c11, c12, c22, c1, c2, b, kappa2);
-                if (c >= L.n) v = -v;
-            } else {
-                v = L.f ? L.f[(long long)node * L.m + (c - nA)] : 0.0;
+                else edge_node(c - L.n4, q, k, l);
+                if (dense || k == i || l == j) {
+                    double v = op_entry(L, i, j, k, l, c11, c12, c22, c1, c2, b, kappa2);
+                    val = (T)(c >= L.n4 ? -v : v);
+                }
+            } else if (c >= nA && L.f) {
+                val = (T)L.f[(long long)node * L.m + (c - nA)];
             }
-            row[c] = (T)v;
+            row[c] = val;
         }
     }
 }
@@ -168,7 +176,7 @@ __device__ void residual(T *__restrict__ M, const double *__restrict__ X, const 
         const double Au = -(c11 * sxx * ux2 + 2.0 * c12 * sxy * uxy + c22 * syy * uy2 + c1 * L.sx * ux1 +
                             c2 * L.sy * uy1) - kappa2 * b * U(i, j);
         const double Bv = (c >= nbd && L.f) ? L.f[(long long)node * L.m + (c - nbd)] : 0.0;
-        M[(long long)rr * L.LDC + L.n + c] = (T)(Bv - Au);
+        M[(long long)rr * L.LDC + L.n4 + c] = (T)(Bv - Au);
     }
 }
 
@@ -220,10 +228,11 @@ __device__ void write_outputs(const CondenseParams &P, int leaf, const LeafInfo 
     }
 }
 
-template <typename T, bool MIXED>
-__global__ void __launch_bounds__(NT) condense_kernel(CondenseParams P) {
+template <typename T, int NB, bool MIXED>
+__global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem sm = carve(smem_raw, P.blk, sizeof(T));
+    const Smem<T> sm = carve<T, NB>(smem_raw, P.blk.ldp);
+    const int ldp = P.blk.ldp;
     unsigned char *slot = P.work + (long long)blockIdx.x * P.slot_bytes;
     T *M = (T *)slot;
     for (;;) {
@@ -240,18 +249,19 @@ __global__ void __launch_bounds__(NT) condense_kernel(CondenseParams P) {
         assemble<T>(M, L, P.kappa2);
         __syncthreads();
         if constexpr (!MIXED) {
-            lu_solve<T>(M, L.LDC, L.n, L.C, true, nullptr, P.blk, sm);
-            write_outputs<T>(P, leaf, L, M + L.n, L.LDC);
+            lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, true, nullptr, ldp, sm);
+            write_outputs<T>(P, leaf, L, M + L.n4, L.LDC);
             __syncthreads();
             if (threadIdx.x == 0) P.info[leaf] = sm.misc[1];
         } else {
             const long long mbytes = (((long long)L.n * L.LDC * (long long)sizeof(T)) + 255) & ~255LL;
             double *X = (double *)(slot + mbytes);
             int *piv_g = (int *)(X + (long long)L.n * L.r);
-            lu_solve<T>(M, L.LDC, L.n, L.C, true, piv_g, P.blk, sm);
-            for (int c = threadIdx.x; c < L.r; c += NT)
-                for (int i = 0; i < L.n; ++i)
-                    X[(long long)i * L.r + c] = (double)M[(long long)i * L.LDC + L.n + c];
+            lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, true, piv_g, ldp, sm);
+            for (long long e = threadIdx.x; e < (long long)L.n * L.r; e += NT) {
+                const int i = (int)(e / L.r), c = (int)(e % L.r);
+                X[e] = (double)M[(long long)i * L.LDC + L.n4 + c];
+            }
             __syncthreads();
             int status = sm.misc[1];
             if (status == 0 && P.kmax > 0) {
@@ -260,12 +270,12 @@ __global__ void __launch_bounds__(NT) condense_kernel(CondenseParams P) {
                 while (!done && it < P.kmax) {
                     residual<T>(M, X, L, P.kappa2);
                     __syncthreads();
-                    lu_solve<T>(M, L.LDC, L.n, L.C, false, piv_g, P.blk, sm);
+                    lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, false, piv_g, ldp, sm);
                     int bad = 0;
                     for (int c = threadIdx.x; c < L.r; c += NT) {
                         double dmax = 0.0, xmax = 0.0;
                         for (int i = 0; i < L.n; ++i) {
-                            const double d = (double)M[(long long)i * L.LDC + L.n + c];
+                            const double d = (double)M[(long long)i * L.LDC + L.n4 + c];
                             const double x = X[(long long)i * L.r + c] + d;
                             X[(long long)i * L.r + c] = x;
                             dmax = fmax(dmax, fabs(d));
@@ -287,13 +297,14 @@ __global__ void __launch_bounds__(NT) condense_kernel(CondenseParams P) {
     }
 }
 
-__global__ void __launch_bounds__(NT) dense_solve_kernel(double *base, long long stride, int n, int C,
-                                                       int LDC, LuBlocking blk, int *info) {
+template <int NB>
+__global__ void __launch_bounds__(NT) dense_solve_kernel(double *base, long long stride, int n, int n4, int C,
+                                                       int LDC, int ldp, int *info) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem sm = carve(smem_raw, blk, sizeof(double));
+    const Smem<double> sm = carve<double, NB>(smem_raw, ldp);
     if (threadIdx.x == 0) sm.misc[1] = 0;
     __syncthreads();
-    lu_solve<double>(base + (long long)blockIdx.x * stride, LDC, n, C, true, nullptr, blk, sm);
+    lu_solve<double, NB>(base + (long long)blockIdx.x * stride, LDC, n, n4, C, true, nullptr, ldp, sm);
     if (threadIdx.x == 0 && info) info[blockIdx.x] = sm.misc[1];
 }
 
@@ -319,47 +330,111 @@ cudaError_t launch_leaf_nodes(const LeafTables &lt, int n_leaves, double *xy, cu
     return cudaGetLastError();
 }
 
-size_t lu_smem_bytes(const LuBlocking &b, size_t tsize) {
-    size_t s = (size_t)b.nb_panel * (b.ldp + b.ch) * tsize;
-    s = (s + 15) & ~(size_t)15;
-    return s + 64 + 64 * 4 + 16 * 4 + 16 * 4;
-}
+namespace {
 
-int condense_max_ctas_per_sm(int prec, size_t smem) {
+template <typename T, int NB>
+size_t smem_of(int ldp) { return smem_bytes_for<T, NB>(ldp); }
+
+template <typename K>
+int occupancy(K kernel, size_t smem) {
     int nb = 0;
-    if (prec == HPS_FP64) {
-        cudaFuncSetAttribute(condense_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, condense_kernel<double, false>, NT, smem);
-    } else {
-        cudaFuncSetAttribute(condense_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, condense_kernel<float, true>, NT, smem);
-    }
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, NT, smem) != cudaSuccess) return 0;
     return nb;
 }
 
-cudaError_t launch_condense_fp64(const CondenseParams &prm, int grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(condense_kernel<double, false>,
+template <typename T, int NB, bool MIXED>
+cudaError_t launch_one(const CondenseParams &prm, int grid, cudaStream_t s) {
+    const size_t smem = smem_of<T, NB>(prm.blk.ldp);
+    cudaError_t e = cudaFuncSetAttribute(condense_kernel<T, NB, MIXED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    condense_kernel<double, false><<<grid, NT, smem, s>>>(prm);
+    condense_kernel<T, NB, MIXED><<<grid, NT, smem, s>>>(prm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dense_solve(double *base, long long stride, int n, int C, int LDC, int batch,
-                               const LuBlocking &blk, int *info, cudaStream_t s) {
-    const size_t smem = lu_smem_bytes(blk, sizeof(double));
-    cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    dense_solve_kernel<<<batch, NT, smem, s>>>(base, stride, n, C, LDC, blk, info);
-    return cudaGetLastError();
+}  // namespace
+
+// Panel width: the widest whose shared memory still allows three CTAs per
+// SM (75 KB), never below 4.
+LuBlocking choose_blocking(int prec, int nmax) {
+    LuBlocking b;
+    b.ldp = panel_ld(nmax);
+    const bool dbl = prec == HPS_FP64;
+    const int cands[3] = {dbl ? 16 : 32, dbl ? 8 : 16, dbl ? 4 : 8};
+    b.nb_panel = cands[2];
+    for (int nb : cands) {
+        const size_t s = dbl ? (nb == 16 ? smem_of<double, 16>(b.ldp) : nb == 8 ? smem_of<double, 8>(b.ldp) : smem_of<double, 4>(b.ldp))
+                             : (nb == 32 ? smem_of<float, 32>(b.ldp) : nb == 16 ? smem_of<float, 16>(b.ldp) : smem_of<float, 8>(b.ldp));
+        if (s <= 75 * 1024) { b.nb_panel = nb; break; }
+    }
+    return b;
 }
 
-cudaError_t launch_condense_mixed32(const CondenseParams &prm, int grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(condense_kernel<float, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    condense_kernel<float, true><<<grid, NT, smem, s>>>(prm);
+size_t condense_smem(int prec, const LuBlocking &b) {
+    if (prec == HPS_FP64)
+        return b.nb_panel == 16 ? smem_of<double, 16>(b.ldp) : b.nb_panel == 8 ? smem_of<double, 8>(b.ldp) : smem_of<double, 4>(b.ldp);
+    return b.nb_panel == 32 ? smem_of<float, 32>(b.ldp) : b.nb_panel == 16 ? smem_of<float, 16>(b.ldp) : smem_of<float, 8>(b.ldp);
+}
+
+int condense_max_ctas_per_sm(int prec, const LuBlocking &b) {
+    const size_t smem = condense_smem(prec, b);
+    if (prec == HPS_FP64) {
+        switch (b.nb_panel) {
+            case 16: return occupancy(condense_kernel<double, 16, false>, smem);
+            case 8: return occupancy(condense_kernel<double, 8, false>, smem);
+            default: return occupancy(condense_kernel<double, 4, false>, smem);
+        }
+    }
+    switch (b.nb_panel) {
+        case 32: return occupancy(condense_kernel<float, 32, true>, smem);
+        case 16: return occupancy(condense_kernel<float, 16, true>, smem);
+        default: return occupancy(condense_kernel<float, 8, true>, smem);
+    }
+}
+
+cudaError_t launch_condense(int prec, const CondenseParams &prm, int grid, cudaStream_t s) {
+    if (prec == HPS_FP64) {
+        switch (prm.blk.nb_panel) {
+            case 16: return launch_one<double, 16, false>(prm, grid, s);
+            case 8: return launch_one<double, 8, false>(prm, grid, s);
+            default: return launch_one<double, 4, false>(prm, grid, s);
+        }
+    }
+    switch (prm.blk.nb_panel) {
+        case 32: return launch_one<float, 32, true>(prm, grid, s);
+        case 16: return launch_one<float, 16, true>(prm, grid, s);
+        default: return launch_one<float, 8, true>(prm, grid, s);
+    }
+}
+
+
+cudaError_t launch_dense_solve(double *base, long long stride, int n, int n4, int C, int LDC, int batch,
+                               int *info, cudaStream_t s) {
+    const int ldp = panel_ld(n);
+    size_t smem = smem_of<double, 16>(ldp);
+    int nb = 16;
+    if (smem > 100 * 1024) { nb = 8; smem = smem_of<double, 8>(ldp); }
+    if (smem > 100 * 1024) { nb = 4; smem = smem_of<double, 4>(ldp); }
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e;
+    switch (nb) {
+        case 16:
+            e = cudaFuncSetAttribute(dense_solve_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            dense_solve_kernel<16><<<batch, NT, smem, s>>>(base, stride, n, n4, C, LDC, ldp, info);
+            break;
+        case 8:
+            e = cudaFuncSetAttribute(dense_solve_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            dense_solve_kernel<8><<<batch, NT, smem, s>>>(base, stride, n, n4, C, LDC, ldp, info);
+            break;
+        default:
+            e = cudaFuncSetAttribute(dense_solve_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            dense_solve_kernel<4><<<batch, NT, smem, s>>>(base, stride, n, n4, C, LDC, ldp, info);
+            break;
+    }
     return cudaGetLastError();
 }
 

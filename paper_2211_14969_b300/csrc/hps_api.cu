@@ -71,20 +71,6 @@ void chebyshev_matrix(int p, std::vector<double> &D) {
     }
 }
 
-LuBlocking choose_blocking(size_t tsize, int nrows, size_t budget) {
-    LuBlocking b;
-    b.ch = 128;
-    b.ldp = nrows | 1;
-    b.nb_panel = 4;
-    for (int nb : {32, 16, 8, 4}) {
-        if ((size_t)nb * (b.ldp + b.ch) * tsize <= budget || nb == 4) {
-            b.nb_panel = nb;
-            break;
-        }
-    }
-    return b;
-}
-
 }  // namespace
 
 struct hps_plan {
@@ -287,14 +273,13 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     const bool mixed = prec != HPS_FP64;
     const size_t tsize = mixed ? sizeof(float) : sizeof(double);
     const int qmax = P->pmax - 2, nmax = qmax * qmax;
-    const LuBlocking blk = choose_blocking(tsize, nmax, 72 * 1024);
-    const size_t smem = lu_smem_bytes(blk, tsize);
-    const int per_sm = condense_max_ctas_per_sm(prec, smem);
+    const LuBlocking blk = choose_blocking(prec, nmax);
+    const int per_sm = condense_max_ctas_per_sm(prec, blk);
     if (per_sm < 1) return P->fail(HPS_ERR_CUDA, "hps_condense: kernel does not fit on an SM");
     const int grid = std::min(P->n_leaves, P->sms * per_sm);
     long long slot = 0;
     for (int p = P->pmin; p <= P->pmax; ++p) {
-        const long long q = p - 2, n = q * q, r = 4 * q + m, C = n + r, LDC = round_up(C, 4);
+        const long long q = p - 2, n = q * q, r = 4 * q + m, C = round_up(n, 4) + r, LDC = round_up(C, 4);
         long long b = n * LDC * (long long)tsize;
         if (mixed) b = round_up(b, 256) + n * r * 8 + n * 4;
         slot = std::max(slot, round_up(b, 256));
@@ -330,7 +315,7 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
         if (evp == nullptr) return P->fail(HPS_ERR_CUDA, "hps_condense: cudaEventCreate failed");
         cudaEventRecord(evp[0], s);
     }
-    e = mixed ? launch_condense_mixed32(prm, grid, smem, s) : launch_condense_fp64(prm, grid, smem, s);
+    e = launch_condense(prec, prm, grid, s);
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense: launch");
     if (evp) {
         cudaEventRecord(evp[1], s);
@@ -468,7 +453,7 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         const size_t oca = put(H.ca), ocb = put(H.cb), opc = put(H.par_child), opi = put(H.par_idx);
         const size_t o3a = put(H.s3a), o3b = put(H.s3b), osa = put(H.srca), osb = put(H.srcb);
         const bool root = li + 1 == hl.size();
-        const int lda = (int)round_up(H.n3 + H.np + m, 4);
+        const int lda = (int)round_up(round_up(H.n3, 4) + H.np + m, 4);
         if ((e = L.maps.ensure(maps.size() * sizeof(int))) != cudaSuccess) break;
         if ((e = L.aug.ensure((size_t)H.nm * H.n3 * lda * sizeof(double))) != cudaSuccess) break;
         if (!root && (e = L.th.ensure((size_t)H.nm * H.np * (H.np + m) * sizeof(double))) != cudaSuccess) break;
@@ -478,7 +463,7 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         const int *mp = (const int *)L.maps.p;
         MergeLevelDev &D = L.dev;
-        D.nm = H.nm; D.n3 = H.n3; D.np = H.np; D.nbc = H.nbc; D.m = m; D.lda = lda;
+        D.nm = H.nm; D.n3 = H.n3; D.c3 = (int)round_up(H.n3, 4); D.np = H.np; D.nbc = H.nbc; D.m = m; D.lda = lda;
         D.ca = mp + oca; D.cb = mp + ocb; D.par_child = mp + opc; D.par_idx = mp + opi;
         D.s3a = mp + o3a; D.s3b = mp + o3b; D.srca = mp + osa; D.srcb = mp + osb;
         D.leaf_T = li == 0 ? d_T : nullptr;
@@ -487,8 +472,7 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         D.aug = (double *)L.aug.p;
         D.Th = root ? nullptr : (double *)L.th.p;
         D.info = (int *)L.info.p;
-        const LuBlocking blk = choose_blocking(sizeof(double), H.n3, 100 * 1024);
-        if ((e = launch_merge_level(D, !root, blk, s)) != cudaSuccess) break;
+        if ((e = launch_merge_level(D, !root, s)) != cudaSuccess) break;
     }
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_merge");
     if ((e = P->u_leaf.ensure((size_t)P->n_leaves * 4 * q * std::max(m, 1) * sizeof(double))) != cudaSuccess)

@@ -8,7 +8,7 @@
 
 namespace hps {
 
-constexpr int kThreads = 256;  // threads per CTA of the condensation kernels
+constexpr int kThreads = 128;  // threads per CTA of the condensation kernels
 
 // Per-leaf device tables, built once per plan.
 struct LeafTables {
@@ -29,12 +29,11 @@ struct DTables {
     const int *doff;  // [HPS_PMAX + 1], -1 where absent
 };
 
-// Blocking of the dense LU: panel width (<= 64), padded panel leading
-// dimension (odd, >= the largest row count) and right-hand chunk width.
+// Blocking of the dense LU: panel width and the leading dimension of the
+// shared-memory panel (>= the largest row count + 8, 4 mod 32).
 struct LuBlocking {
     int nb_panel;
     int ldp;
-    int ch;
 };
 
 struct CondenseParams {
@@ -56,15 +55,16 @@ struct CondenseParams {
 };
 
 // Host-side launchers (condense.cu).
-cudaError_t launch_condense_fp64(const CondenseParams &prm, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_condense_mixed32(const CondenseParams &prm, int grid, size_t smem, cudaStream_t s);
-size_t lu_smem_bytes(const LuBlocking &b, size_t tsize);
+LuBlocking choose_blocking(int prec, int nmax);
+size_t condense_smem(int prec, const LuBlocking &b);
+int condense_max_ctas_per_sm(int prec, const LuBlocking &b);
+cudaError_t launch_condense(int prec, const CondenseParams &prm, int grid, cudaStream_t s);
 cudaError_t launch_leaf_nodes(const LeafTables &lt, int n_leaves, double *xy, cudaStream_t s);
-int condense_max_ctas_per_sm(int prec, size_t smem);
 
-// Batched dense solves [A | RHS] -> [LU | X] (one CTA per system), used by
-// the merges: system s at base + s * stride (elements), row-major, ld LDC.
-cudaError_t launch_dense_solve(double *base, long long stride, int n, int C, int LDC, int batch,
-                               const LuBlocking &blk, int *info, cudaStream_t s);
+// Batched dense solves [A | 0 | RHS] -> [LU | 0 | X] (one CTA per system),
+// used by the merges: system s at base + s * stride (elements), row-major,
+// ld LDC, A of n columns, right-hand side from column n4 = round4(n).
+cudaError_t launch_dense_solve(double *base, long long stride, int n, int n4, int C, int LDC, int batch,
+                               int *info, cudaStream_t s);
 
 }  // namespace hps

@@ -42,13 +42,13 @@ __device__ __forceinline__ ChildView child_view(const MergeLevelDev &L, int chil
     return v;
 }
 
-// Aug[s] = [Z | -[Ta31 Tb32] (parent column order) | -(ha3 + hb3)].
+// Aug[s] = [Z | 0 | -[Ta31 Tb32] (parent column order) | -(ha3 + hb3)].
 __global__ void merge_build_aug(MergeLevelDev L) {
     const int s = blockIdx.y;
     const ChildView A = child_view(L, L.ca[s]);
     const ChildView B = child_view(L, L.cb[s]);
     double *aug = L.aug + (long long)s * L.n3 * L.lda;
-    const int C = L.n3 + L.np + L.m;
+    const int C = L.c3 + L.np + L.m;
     for (long long e = blockIdx.x * (long long)NT + threadIdx.x; e < (long long)L.n3 * C;
          e += (long long)gridDim.x * NT) {
         const int k = (int)(e / C), c = (int)(e % C);
@@ -56,12 +56,14 @@ __global__ void merge_build_aug(MergeLevelDev L) {
         double v;
         if (c < L.n3) {
             v = A.T[(long long)ra * A.ld + L.s3a[c]] + B.T[(long long)rb * B.ld + L.s3b[c]];
-        } else if (c < L.n3 + L.np) {
-            const int P = c - L.n3;
+        } else if (c < L.c3) {
+            v = 0.0;
+        } else if (c < L.c3 + L.np) {
+            const int P = c - L.c3;
             const int idx = L.par_idx[P];
             v = L.par_child[P] == 0 ? -A.T[(long long)ra * A.ld + idx] : -B.T[(long long)rb * B.ld + idx];
         } else {
-            const int cc = c - L.n3 - L.np;
+            const int cc = c - L.c3 - L.np;
             v = -(A.h[(long long)ra * A.ldh + cc] + B.h[(long long)rb * B.ldh + cc]);
         }
         aug[(long long)k * L.lda + c] = v;
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(NT) merge_parent(MergeLevelDev L) {
         for (int e = threadIdx.x; e < BK * BN; e += NT) {
             const int kk = e / BN, cc = e % BN;
             const int k = k0 + kk, c = c0 + cc;
-            Bs[kk][cc] = (k < L.n3 && c < ldt) ? aug[(long long)k * L.lda + L.n3 + c] : 0.0;
+            Bs[kk][cc] = (k < L.n3 && c < ldt) ? aug[(long long)k * L.lda + L.c3 + c] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -138,7 +140,7 @@ __global__ void merge_down(MergeLevelDev L, const double *__restrict__ upar, dou
     const double *up = upar + (long long)s * L.np * L.m;
     for (int e = threadIdx.x; e < L.n3 * L.m; e += NT) {
         const int k = e / L.m, c = e % L.m;
-        const double *row = aug + (long long)k * L.lda + L.n3;
+        const double *row = aug + (long long)k * L.lda + L.c3;
         double acc = row[L.np + c];
         for (int P = 0; P < L.np; ++P) acc = fma(row[P], up[(long long)P * L.m + c], acc);
         u3[e] = acc;
@@ -187,16 +189,15 @@ __global__ void leaf_recover(int p, int m, const double *__restrict__ S, const d
 
 }  // namespace
 
-cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, const LuBlocking &blk,
-                               cudaStream_t s) {
-    const int C = L.n3 + L.np + L.m;
+cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s) {
+    const int C = L.c3 + L.np + L.m;
     long long work = (long long)L.n3 * C;
     int gx = (int)((work + NT - 1) / NT);
     if (gx > 1024) gx = 1024;
     merge_build_aug<<<dim3(gx, L.nm), NT, 0, s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_dense_solve(L.aug, (long long)L.n3 * L.lda, L.n3, C, L.lda, L.nm, blk, L.info, s);
+    e = launch_dense_solve(L.aug, (long long)L.n3 * L.lda, L.n3, L.c3, C, L.lda, L.nm, L.info, s);
     if (e != cudaSuccess) return e;
     if (form_parent) {
         const int ldt = L.np + L.m;

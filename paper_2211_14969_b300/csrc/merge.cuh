@@ -10,6 +10,7 @@ namespace hps {
 struct MergeLevelDev {
     int nm;    // merges at this level
     int n3;    // shared-edge nodes per merge
+    int c3;    // first right-hand column of the augmented systems (round4(n3))
     int np;    // parent boundary nodes
     int nbc;   // child boundary nodes
     int m;     // body-load columns
@@ -20,13 +21,12 @@ struct MergeLevelDev {
     const int *srca, *srcb;          // [nbc] child node -> parent node, or -(k+1) for shared node k
     const double *leaf_T, *leaf_h;   // children are leaves (level 0), else null
     const double *prev_Th;           // children's [T | h] (ld nbc + m)
-    double *aug;                     // [nm][n3][lda]: [Z | S3 | w3] after the solve
+    double *aug;                     // [nm][n3][lda]: [Z | 0 | S3 | w3] after the solve
     double *Th;                      // [nm][np][np + m]: parent [T | h]
     int *info;                       // [nm] zero-pivot step of Z (0 = none)
 };
 
-cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, const LuBlocking &blk,
-                               cudaStream_t s);
+cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s);
 cudaError_t launch_merge_down(const MergeLevelDev &L, const double *upar, double *uchild, cudaStream_t s);
 cudaError_t launch_leaf_recover(int n_leaves, int p, int m, const double *S, const double *W,
                                 const double *ub, double *u, cudaStream_t s);
