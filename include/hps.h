@@ -102,9 +102,14 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
  *                  hold inf/NaN),
  *            -k    mixed precision: refinement did not reach tol in k steps.
  * prec: HPS_FP64 or HPS_MIXED_FP32 (others return HPS_ERR_ARG for now).
- * tol, kmax: refinement stops when every correction is below tol relative
- *            to the solution (max norm per column), after at most kmax
- *            corrections; ignored for HPS_FP64.
+ *       HPS_MIXED_FP32 needs 4(p-2) + m <= 256 for the largest p.
+ * tol, kmax: iterative refinement with FP64 residuals.  Per right-hand column
+ *            let eta_k = max|correction_k| / max|X| (eta_0 = 1); the error
+ *            left after correction k is estimated as eta_k^2 / eta_{k-1}
+ *            (linear convergence).  Refinement stops once every column's
+ *            estimate is <= tol while still contracting, or after kmax
+ *            corrections (then info = -kmax).  kmax = 0 returns the FP32
+ *            solution unrefined.  Ignored for HPS_FP64.
  * Corner rows: with c12 != 0 the interior rows touch the leaf corners, whose
  * columns are dropped (corners are not unknowns). */
 hps_status hps_condense(hps_plan *plan, hps_prec prec, const double *d_coef, const double *d_f,

@@ -27,17 +27,6 @@ namespace {
 
 using namespace lu;
 
-// Node (k, l) of the n_b-th edge node: edges [W, E, S, N], each by
-// increasing coordinate, corners excluded.
-__device__ __forceinline__ void edge_node(int t, int q, int &k, int &l) {
-    const int e = t / q, s = t % q + 1;
-    const int pm1 = q + 1;
-    if (e == 0) { k = 0; l = s; }
-    else if (e == 1) { k = pm1; l = s; }
-    else if (e == 2) { k = s; l = 0; }
-    else { k = s; l = pm1; }
-}
-
 struct LeafInfo {
     int p, q, n, n4, nbd, m, r, C, LDC;
     double sx, sy;
@@ -84,148 +73,387 @@ __device__ int leaf_flags(const LeafInfo &L) {
     return (a ? 1 : 0) | (b ? 2 : 0) | (c ? 4 : 0);
 }
 
-// Collocation operator entry A[(i,j),(k,l)] of
-//   -(c11 u_xx + 2 c12 u_xy + c22 u_yy + c1 u_x + c2 u_y) - kappa^2 b u.
-__device__ __forceinline__ double op_entry(const LeafInfo &L, int i, int j, int k, int l,
-                                           double c11, double c12, double c22, double c1,
-                                           double c2, double b, double kappa2) {
-    const int p = L.p;
-    double v = 0.0;
-    if (l == j) v += c11 * L.sx * L.sx * L.D2[i * p + k] + c1 * L.sx * L.D[i * p + k];
-    if (k == i) v += c22 * L.sy * L.sy * L.D2[j * p + l] + c2 * L.sy * L.D[j * p + l];
-    if (L.flags & 1) v += 2.0 * c12 * L.sx * L.sy * L.D[i * p + k] * L.D[j * p + l];
-    v = -v;
-    if (k == i && l == j) v -= kappa2 * b;
-    return v;
+// float <-> double conversions done with integer operations on the bit
+// patterns (IEEE 754 binary32 / binary64 layouts), so the refinement loop
+// does not queue conversions behind the FP64 arithmetic.  Values outside the
+// normal range take the conversion instruction.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) {
+        if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+        return (double)f;
+    }
+    const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned long long ex = (unsigned long long)(e + (1023u - 127u)) << 52;
+    const unsigned long long mt = (unsigned long long)(u & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(s | ex | mt));
 }
 
-// M (row-major, ld LDC) <- [A_ii | 0 | -A_ib | f_I].  Entries that are
-// structurally zero (no shared grid line, c12 == 0) are written without
-// any FP64 arithmetic.
+// double -> float keeping the leading 24 significant bits (truncation; a
+// relative change below 2^-23 of a residual is immaterial to the correction
+// it drives).
+__device__ __forceinline__ float d2f_trunc(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    if ((u << 1) == 0ull) return __uint_as_float((unsigned)(u >> 32));
+    const int e = (int)((u >> 52) & 0x7ffull) - 1023 + 127;
+    if (e <= 0 || e >= 0xff) return (float)d;
+    const unsigned s = (unsigned)(u >> 32) & 0x80000000u;
+    const unsigned mt = (unsigned)((u >> 29) & 0x7fffffull);
+    return __uint_as_float(s | ((unsigned)e << 23) | mt);
+}
+
+
+// Edge-node index of grid node (k, l) on the leaf boundary (not a corner).
+__device__ __forceinline__ int edge_index(int k, int l, int p, int q) {
+    return (k == 0) ? (l - 1) : (k == p - 1) ? (q + l - 1) : (l == 0) ? (2 * q + k - 1) : (3 * q + k - 1);
+}
+
+// M (row-major, ld LDC) <- [A_ii | 0 | -A_ib | f_I] for the operator
+//   -(c11 u_xx + 2 c12 u_xy + c22 u_yy + c1 u_x + c2 u_y) - kappa^2 b u,
+// one warp per row.  The row is zeroed, then only the nodes that share a
+// grid line with the row's node are written (all nodes when c12 != 0).  The
+// entries are formed in the working precision from per-row factors and the
+// differentiation matrices held in that precision.
 template <typename T>
-__device__ void assemble(T *__restrict__ M, const LeafInfo &L, double kappa2) {
+__device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restrict__ Dw, double kappa2) {
+    using V = typename Vec<T>::type;
+    constexpr int HV = Vec<T>::N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = L.p, q = L.q, p2 = p * p, nA = L.n4 + L.nbd;
+    const T *D2w = Dw + p2;
     const bool dense = (L.flags & 1) != 0;
     for (int rr = warp; rr < L.n; rr += NWARP) {
-        const int i = rr / q + 1, j = rr % q + 1, node = i * p + j;
+        const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
         const double c11 = L.coef[node], c12 = L.coef[p2 + node], c22 = L.coef[2 * p2 + node];
         const double c1 = L.coef[3 * p2 + node], c2 = L.coef[4 * p2 + node];
         const double b = L.coef[5 * p2 + node];
+        const T ax2 = (T)(c11 * L.sx * L.sx), ax1 = (T)(c1 * L.sx);
+        const T ay2 = (T)(c22 * L.sy * L.sy), ay1 = (T)(c2 * L.sy);
+        const T axy = (T)(2.0 * c12 * L.sx * L.sy), dg = (T)(kappa2 * b);
         T *row = M + (long long)rr * L.LDC;
-        for (int c = lane; c < L.C; c += 32) {
-            T val = T(0);
-            if (c < L.n || (c >= L.n4 && c < nA)) {
-                int k, l;
-                if (c < L.n) { k = c / q + 1; l = c % q + 1; }
-                else edge_node(c - L.n4, q, k, l);
-                if (dense || k == i || l == j) {
-                    double v = op_entry(L, i, j, k, l, c11, c12, c22, c1, c2, b, kappa2);
-                    val = (T)(c >= L.n4 ? -v : v);
-                }
-            } else if (c >= nA && L.f) {
-                val = (T)L.f[(long long)node * L.m + (c - nA)];
+        V zero;
+        T *zp = (T *)&zero;
+#pragma unroll
+        for (int v = 0; v < HV; ++v) zp[v] = T(0);
+        for (int c = lane * HV; c < L.LDC; c += 32 * HV) *(V *)(row + c) = zero;
+        __syncwarp();
+        // entry of column node (k, l): -(x-line + y-line + mixed) - kappa^2 b on the diagonal
+        auto entry = [&](int k, int l) -> T {
+            T v = T(0);
+            if (l == j) v += ax2 * D2w[i * p + k] + ax1 * Dw[i * p + k];
+            if (k == i) v += ay2 * D2w[j * p + l] + ay1 * Dw[j * p + l];
+            if (dense) v += axy * Dw[i * p + k] * Dw[j * p + l];
+            v = -v;
+            if (k == i && l == j) v -= dg;
+            return v;
+        };
+        auto put = [&](int k, int l) {
+            const bool bk = (k == 0 || k == p - 1), bl = (l == 0 || l == p - 1);
+            if (bk && bl) return;  // corners are not unknowns
+            const T v = entry(k, l);
+            if (!bk && !bl) row[(k - 1) * q + (l - 1)] = v;
+            else row[L.n4 + edge_index(k, l, p, q)] = -v;
+        };
+        if (!dense) {
+            for (int t = lane; t < 2 * p; t += 32) {
+                if (t < p) put(t, j);                       // the x-line through (i, j)
+                else if (t - p != j) put(i, t - p);         // the y-line, diagonal already written
             }
-            row[c] = val;
+        } else {
+            for (int k = 0; k < p; ++k)
+                for (int l = lane; l < p; l += 32) put(k, l);
+        }
+        if (L.f)
+            for (int c = lane; c < L.m; c += 32) row[nA + c] = (T)L.f[(long long)node * L.m + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (a value carried as an unevaluated sum hi + lo of
+// two floats), built from the error-free transformations TwoSum (Knuth) and
+// FMA-based TwoProd (Dekker / Ogita-Rump-Oishi 2005).  About 48 significant
+// bits, on the FP32 pipe.
+// ---------------------------------------------------------------------------
+struct DF { float hi, lo; };
+
+// The _rn intrinsics are never contracted into FMAs, which would break the
+// exactness these transformations rely on.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ DF df_from(double x) {
+    DF r;
+    r.hi = d2f_trunc(x);
+    r.lo = d2f_trunc(x - f2d(r.hi));
+    return r;
+}
+
+// acc += a * u (a, u double-float; acc kept as hi + lo, lo unnormalised)
+__device__ __forceinline__ void df_mac(DF &acc, float ah, float al, float uh, float ul) {
+    const float ph = __fmul_rn(ah, uh);
+    float pe = fmaf(ah, uh, -ph);
+    pe = fmaf(ah, ul, pe);
+    pe = fmaf(al, uh, pe);
+    float s, se;
+    two_sum(acc.hi, ph, s, se);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(se, pe));
+}
+
+__device__ __forceinline__ DF df_norm(DF a) {
+    DF r;
+    r.hi = __fadd_rn(a.hi, a.lo);
+    r.lo = __fsub_rn(a.lo, __fsub_rn(r.hi, a.hi));
+    return r;
+}
+
+// Per interior node: the operator factors c11 sx^2, c1 sx, c22 sy^2, c2 sy,
+// 2 c12 sx sy, kappa^2 b and the body loads are fixed for a leaf; they are
+// formed once in FP64 and stored as double-float pairs (12 floats a node).
+__device__ void node_factors(const LeafInfo &L, double kappa2, float *__restrict__ nf) {
+    const int p = L.p, q = L.q, p2 = p * p;
+    for (int rr = threadIdx.x; rr < L.n; rr += NT) {
+        const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
+        const double v[6] = {L.coef[node] * L.sx * L.sx, L.coef[3 * p2 + node] * L.sx,
+                             L.coef[2 * p2 + node] * L.sy * L.sy, L.coef[4 * p2 + node] * L.sy,
+                             2.0 * L.coef[p2 + node] * L.sx * L.sy, kappa2 * L.coef[5 * p2 + node]};
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const DF d = df_from(v[t]);
+            nf[rr * 12 + 2 * t] = d.hi;
+            nf[rr * 12 + 2 * t + 1] = d.lo;
         }
     }
 }
 
-// R = B - A_ii X in FP64, applied matrix-free: for column c the grid
-// function holds X[:, c] at the interior nodes, the unit vector of edge node
-// c (c < n_b) or zero (c >= n_b) on the edges, zero at the corners; B is 0
-// for c < n_b (the -A_ib e_c term is inside A applied to that grid) and f_I
-// otherwise.  Written to M[:, n + c] in the working type.
+// R = B - A_ii X, applied matrix-free in double-float arithmetic: for column
+// c the grid function holds X[:, c] at the interior nodes, the unit vector of
+// edge node c (c < n_b) or zero (c >= n_b) on the edges, zero at the
+// corners; B is 0 for c < n_b (the -A_ib e_c term is inside A applied to
+// that grid) and f_I otherwise.  Written to M[:, n4 + c] in the working
+// type.
+// Columns go in chunks of cw, staged in shared memory as hi/lo float pairs
+// (Xs, n x cwp, cwp = cw rounded up to 4); D and D^2 are staged as pairs in
+// Dp.  Each thread takes one interior node and 4 columns, so the four sums
+// of a line are independent chains sharing the D loads.
 template <typename T>
 __device__ void residual(T *__restrict__ M, const double *__restrict__ X, const LeafInfo &L,
-                         double kappa2) {
-    const int p = L.p, q = L.q, p2 = p * p, r = L.r, nbd = L.nbd;
-    const double sxx = L.sx * L.sx, syy = L.sy * L.sy, sxy = L.sx * L.sy;
-    for (long long e = threadIdx.x; e < (long long)L.n * r; e += NT) {
-        const int rr = (int)(e / r), c = (int)(e % r);
-        const int i = rr / q + 1, j = rr % q + 1, node = i * p + j;
-        auto U = [&](int k, int l) -> double {
-            if (k >= 1 && k <= q && l >= 1 && l <= q) return X[(long long)((k - 1) * q + (l - 1)) * r + c];
-            if (c >= nbd) return 0.0;
-            if ((k == 0 || k == p - 1) && (l == 0 || l == p - 1)) return 0.0;
-            const int bi = (k == 0) ? (l - 1) : (k == p - 1) ? (q + l - 1) : (l == 0) ? (2 * q + k - 1) : (3 * q + k - 1);
-            return bi == c ? 1.0 : 0.0;
-        };
-        double ux2 = 0.0, ux1 = 0.0, uy2 = 0.0, uy1 = 0.0, uxy = 0.0;
-        const double *Di = L.D + i * p, *D2i = L.D2 + i * p;
-        const double *Dj = L.D + j * p, *D2j = L.D2 + j * p;
-        for (int k = 0; k < p; ++k) {
-            const double u = U(k, j);
-            ux2 = fma(D2i[k], u, ux2);
-            if (L.flags & 2) ux1 = fma(Di[k], u, ux1);
+                         const float *__restrict__ Dh, const float *__restrict__ Dl,
+                         const float *__restrict__ nf, float2 *__restrict__ Xs, float2 *__restrict__ Dp,
+                         int cw_max) {
+    constexpr int G = 4;
+    const int p = L.p, q = L.q, r = L.r, nbd = L.nbd, n = L.n, p2 = p * p;
+    for (int e = threadIdx.x; e < 2 * p2; e += NT) Dp[e] = make_float2(Dh[e], Dl[e]);
+    const float2 *Dq = Dp, *D2q = Dp + p2;
+    for (int c0 = 0; c0 < r; c0 += cw_max) {
+        const int cw = min(cw_max, r - c0), cwp = (cw + 3) & ~3, ng = cwp / G;
+        for (int e = threadIdx.x; e < n * cwp; e += NT) {
+            const int i = e / cwp, cc = e - i * cwp;
+            DF d = {0.0f, 0.0f};
+            if (cc < cw) d = df_from(X[(long long)i * r + c0 + cc]);
+            Xs[e] = make_float2(d.hi, d.lo);
         }
-        for (int l = 0; l < p; ++l) {
-            const double u = U(i, l);
-            uy2 = fma(D2j[l], u, uy2);
-            if (L.flags & 4) uy1 = fma(Dj[l], u, uy1);
-        }
-        if (L.flags & 1) {
-            for (int k = 0; k < p; ++k) {
-                double s = 0.0;
-                for (int l = 0; l < p; ++l) s = fma(Dj[l], U(k, l), s);
-                uxy = fma(Di[k], s, uxy);
+        __syncthreads();
+        for (int w = threadIdx.x; w < n * ng; w += NT) {
+            const int rr = w / ng, g = w - rr * ng;
+            const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
+            DF ax2[G], ax1[G], ay2[G], ay1[G], axy[G];
+#pragma unroll
+            for (int t = 0; t < G; ++t) ax2[t] = ax1[t] = ay2[t] = ay1[t] = axy[t] = DF{0.0f, 0.0f};
+            // x-line interior: nodes (k, j), k = 1..q, stride q rows of Xs
+            {
+                const float4 *xp = (const float4 *)(Xs + (j - 1) * cwp + g * G);
+                const int stride = q * cwp / 2;   // in float4 units (two pairs each)
+                for (int k = 1; k <= q; ++k, xp += stride) {
+                    const float4 u01 = xp[0], u23 = xp[1];
+                    const float2 d2 = D2q[i * p + k];
+                    df_mac(ax2[0], d2.x, d2.y, u01.x, u01.y);
+                    df_mac(ax2[1], d2.x, d2.y, u01.z, u01.w);
+                    df_mac(ax2[2], d2.x, d2.y, u23.x, u23.y);
+                    df_mac(ax2[3], d2.x, d2.y, u23.z, u23.w);
+                    if (L.flags & 2) {
+                        const float2 d1 = Dq[i * p + k];
+                        df_mac(ax1[0], d1.x, d1.y, u01.x, u01.y);
+                        df_mac(ax1[1], d1.x, d1.y, u01.z, u01.w);
+                        df_mac(ax1[2], d1.x, d1.y, u23.x, u23.y);
+                        df_mac(ax1[3], d1.x, d1.y, u23.z, u23.w);
+                    }
+                }
+            }
+            // y-line interior: nodes (i, l), l = 1..q, consecutive rows of Xs
+            {
+                const float4 *xp = (const float4 *)(Xs + (i - 1) * q * cwp + g * G);
+                const int stride = cwp / 2;
+                for (int l = 1; l <= q; ++l, xp += stride) {
+                    const float4 u01 = xp[0], u23 = xp[1];
+                    const float2 d2 = D2q[j * p + l];
+                    df_mac(ay2[0], d2.x, d2.y, u01.x, u01.y);
+                    df_mac(ay2[1], d2.x, d2.y, u01.z, u01.w);
+                    df_mac(ay2[2], d2.x, d2.y, u23.x, u23.y);
+                    df_mac(ay2[3], d2.x, d2.y, u23.z, u23.w);
+                    if (L.flags & 4) {
+                        const float2 d1 = Dq[j * p + l];
+                        df_mac(ay1[0], d1.x, d1.y, u01.x, u01.y);
+                        df_mac(ay1[1], d1.x, d1.y, u01.z, u01.w);
+                        df_mac(ay1[2], d1.x, d1.y, u23.x, u23.y);
+                        df_mac(ay1[3], d1.x, d1.y, u23.z, u23.w);
+                    }
+                }
+            }
+            // edge nodes on the two lines carry the unit value of their column
+            const int ew = j - 1, ee = q + j - 1, es = 2 * q + i - 1, en = 3 * q + i - 1;
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const int c = c0 + g * G + t;
+                if (c >= nbd) continue;
+                if (c == ew) { df_mac(ax2[t], D2q[i * p].x, D2q[i * p].y, 1.0f, 0.0f); df_mac(ax1[t], Dq[i * p].x, Dq[i * p].y, 1.0f, 0.0f); }
+                if (c == ee) { df_mac(ax2[t], D2q[i * p + p - 1].x, D2q[i * p + p - 1].y, 1.0f, 0.0f); df_mac(ax1[t], Dq[i * p + p - 1].x, Dq[i * p + p - 1].y, 1.0f, 0.0f); }
+                if (c == es) { df_mac(ay2[t], D2q[j * p].x, D2q[j * p].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p].x, Dq[j * p].y, 1.0f, 0.0f); }
+                if (c == en) { df_mac(ay2[t], D2q[j * p + p - 1].x, D2q[j * p + p - 1].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p + p - 1].x, Dq[j * p + p - 1].y, 1.0f, 0.0f); }
+            }
+            if (L.flags & 1) {   // mixed derivative: every node of the leaf
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int cc = g * G + t, c = c0 + cc;
+                    if (cc >= cw) continue;
+                    auto U = [&](int k, int l) -> float2 {
+                        if (k >= 1 && k <= q && l >= 1 && l <= q) return Xs[((k - 1) * q + (l - 1)) * cwp + cc];
+                        if (c >= nbd || ((k == 0 || k == p - 1) && (l == 0 || l == p - 1))) return make_float2(0.0f, 0.0f);
+                        return make_float2(edge_index(k, l, p, q) == c ? 1.0f : 0.0f, 0.0f);
+                    };
+                    for (int k = 0; k < p; ++k) {
+                        DF sk = {0.0f, 0.0f};
+                        for (int l = 0; l < p; ++l) {
+                            const float2 u = U(k, l);
+                            df_mac(sk, Dq[j * p + l].x, Dq[j * p + l].y, u.x, u.y);
+                        }
+                        sk = df_norm(sk);
+                        df_mac(axy[t], Dq[i * p + k].x, Dq[i * p + k].y, sk.hi, sk.lo);
+                    }
+                }
+            }
+            // A u = -(a2x ux2 + a1x ux1 + a2y uy2 + a1y uy1 + axy uxy) - dg u_ij;
+            // R = B - A u with B = f for load columns
+            const float *f6 = nf + rr * 12;
+            const float4 *xij = (const float4 *)(Xs + rr * cwp + g * G);
+            const float4 u01 = xij[0], u23 = xij[1];
+            const float2 uij[G] = {make_float2(u01.x, u01.y), make_float2(u01.z, u01.w), make_float2(u23.x, u23.y),
+                                   make_float2(u23.z, u23.w)};
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const int cc = g * G + t, c = c0 + cc;
+                if (cc >= cw) continue;
+                DF au = {0.0f, 0.0f};
+                const DF t0 = df_norm(ax2[t]), t1 = df_norm(ax1[t]), t2 = df_norm(ay2[t]), t3 = df_norm(ay1[t]),
+                         t4 = df_norm(axy[t]);
+                df_mac(au, f6[0], f6[1], t0.hi, t0.lo);
+                df_mac(au, f6[2], f6[3], t1.hi, t1.lo);
+                df_mac(au, f6[4], f6[5], t2.hi, t2.lo);
+                df_mac(au, f6[6], f6[7], t3.hi, t3.lo);
+                df_mac(au, f6[8], f6[9], t4.hi, t4.lo);
+                df_mac(au, f6[10], f6[11], uij[t].x, uij[t].y);
+                if (c >= nbd && L.f) {
+                    const DF b = df_from(L.f[(long long)node * L.m + (c - nbd)]);
+                    float s2, se;
+                    two_sum(au.hi, b.hi, s2, se);
+                    au.hi = s2;
+                    au.lo = __fadd_rn(au.lo, __fadd_rn(se, b.lo));
+                }
+                M[(long long)rr * L.LDC + L.n4 + c] = (T)__fadd_rn(au.hi, au.lo);
             }
         }
-        const double c11 = L.coef[node], c12 = L.coef[p2 + node], c22 = L.coef[2 * p2 + node];
-        const double c1 = L.coef[3 * p2 + node], c2 = L.coef[4 * p2 + node], b = L.coef[5 * p2 + node];
-        const double Au = -(c11 * sxx * ux2 + 2.0 * c12 * sxy * uxy + c22 * syy * uy2 + c1 * L.sx * ux1 +
-                            c2 * L.sy * uy1) - kappa2 * b * U(i, j);
-        const double Bv = (c >= nbd && L.f) ? L.f[(long long)node * L.m + (c - nbd)] : 0.0;
-        M[(long long)rr * L.LDC + L.n4 + c] = (T)(Bv - Au);
+        __syncthreads();
     }
 }
 
 // S, W from X (FP64 values, row-major, ld ldx); T and h by the DtN rows:
 // the outward normal derivative at edge node a is a combination of the
 // nodes on the grid line through it (Section 2: flux on element boundaries).
+// Rows by warp, columns by lane.
 template <typename XT>
 __device__ void write_outputs(const CondenseParams &P, int leaf, const LeafInfo &L,
                               const XT *__restrict__ X, int ldx) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int q = L.q, p = L.p, n = L.n, nbd = L.nbd, m = L.m, r = L.r;
-    if (P.S) {
-        double *S = P.S + P.lt.o_sb[leaf];
-        for (long long e = threadIdx.x; e < (long long)n * nbd; e += NT) {
-            const int i = (int)(e / nbd), b = (int)(e % nbd);
-            S[e] = (double)X[(long long)i * ldx + b];
-        }
-    }
-    if (P.W && m > 0) {
-        double *W = P.W + P.lt.o_ni[leaf] * m;
-        for (long long e = threadIdx.x; e < (long long)n * m; e += NT) {
-            const int i = (int)(e / m), c = (int)(e % m);
-            W[e] = (double)X[(long long)i * ldx + nbd + c];
-        }
+    double *S = P.S ? P.S + P.lt.o_sb[leaf] : nullptr;
+    double *W = (P.W && m > 0) ? P.W + P.lt.o_ni[leaf] * m : nullptr;
+    for (int i = warp; i < n; i += NWARP) {
+        const XT *xr = X + (long long)i * ldx;
+        if (S)
+            for (int b = lane; b < nbd; b += 32) S[(long long)i * nbd + b] = (double)xr[b];
+        if (W)
+            for (int cc = lane; cc < m; cc += 32) W[(long long)i * m + cc] = (double)xr[nbd + cc];
     }
     double *Tm = P.T + P.lt.o_bb[leaf];
     double *hm = (m > 0 && P.h) ? P.h + P.lt.o_nb[leaf] * m : nullptr;
-    for (int e = threadIdx.x; e < nbd * r; e += NT) {
-        const int a = e / r, b = e % r;
-        const int edge = a / q, s = a % q;
+    for (int a = warp; a < nbd; a += NWARP) {
+        const int edge = a / q, s = a - edge * q;
         const bool far = (edge & 1);              // E or N: derivative row p-1
-        const double sgn = far ? 1.0 : -1.0;
-        const double scl = sgn * ((edge < 2) ? L.sx : L.sy);
+        const double scl = (far ? 1.0 : -1.0) * ((edge < 2) ? L.sx : L.sy);
         const double *Drow = L.D + (far ? (p - 1) * p : 0);
-        double acc = 0.0;
-        if (edge < 2) {
-            for (int k = 1; k <= q; ++k) acc = fma(Drow[k], (double)X[(long long)((k - 1) * q + s) * ldx + b], acc);
-        } else {
-            for (int l = 1; l <= q; ++l) acc = fma(Drow[l], (double)X[(long long)(s * q + (l - 1)) * ldx + b], acc);
-        }
-        acc *= scl;
-        if (b < nbd) {
-            const int opp = (edge ^ 1) * q + s;   // edge node on the same line, other side
-            if (b == a) acc += scl * Drow[far ? p - 1 : 0];
-            if (b == opp) acc += scl * Drow[far ? 0 : p - 1];
-            Tm[(long long)a * nbd + b] = acc;
-        } else if (hm) {
-            hm[(long long)a * m + (b - nbd)] = acc;
+        // interior nodes on the line: (k, s+1) for W/E, (s+1, l) for S/N
+        const long long base = (edge < 2) ? s : (long long)s * q;
+        const long long step = (edge < 2) ? q : 1;
+        const int opp = (edge ^ 1) * q + s;   // edge node on the same line, other side
+        for (int b = lane; b < r; b += 32) {
+            double acc = 0.0;
+            for (int k = 1; k <= q; ++k) acc = fma(Drow[k], (double)X[(base + (k - 1) * step) * ldx + b], acc);
+            acc *= scl;
+            if (b < nbd) {
+                if (b == a) acc += scl * Drow[far ? p - 1 : 0];
+                if (b == opp) acc += scl * Drow[far ? 0 : p - 1];
+                Tm[(long long)a * nbd + b] = acc;
+            } else if (hm) {
+                hm[(long long)a * m + (b - nbd)] = acc;
+            }
         }
     }
+}
+
+// X (FP64, n x r) += correction in M[:, n4..]; returns (block-uniform)
+// whether every column's estimated error after this correction is <= tol.
+// eta[c] holds the previous relative correction of column c (1 before the
+// first); the estimate for linearly converging refinement is
+// eta_k^2 / eta_{k-1}, and a column that stopped contracting never passes.
+template <typename T>
+__device__ bool refine_update(T *__restrict__ M, double *__restrict__ X, float *__restrict__ eta,
+                              const LeafInfo &L, double tol, unsigned *colmax) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = L.r;
+    for (int c = threadIdx.x; c < 2 * r; c += NT) colmax[c] = 0u;
+    __syncthreads();
+    for (int c0 = 0; c0 < r; c0 += 32) {
+        const int c = c0 + lane;
+        float dmax = 0.0f, xmax = 0.0f;
+        if (c < r) {
+            for (int i = warp; i < L.n; i += NWARP) {
+                const T d = M[(long long)i * L.LDC + L.n4 + c];
+                const double x = X[(long long)i * r + c] + f2d((float)d);
+                X[(long long)i * r + c] = x;
+                dmax = fmaxf(dmax, fabsf((float)d));
+                xmax = fmaxf(xmax, fabsf(d2f_trunc(x)));
+            }
+            // non-negative floats order like their bit patterns; NaN maps high
+            atomicMax(&colmax[c], dmax == dmax ? __float_as_uint(dmax) : 0x7f800000u);
+            atomicMax(&colmax[r + c], __float_as_uint(xmax));
+        }
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int c = threadIdx.x; c < r; c += NT) {
+        const float dmax = __uint_as_float(colmax[c]), xmax = __uint_as_float(colmax[r + c]);
+        const float e_k = xmax > 0.0f ? dmax / xmax : (dmax > 0.0f ? 1.0f : 0.0f);
+        const float e_prev = eta[c];
+        const bool contracting = e_k < e_prev || e_k == 0.0f;
+        const double est = e_prev > 0.0f ? (double)e_k * (double)e_k / (double)e_prev : 0.0;
+        if (!(contracting && est <= tol)) bad = 1;
+        eta[c] = e_k;
+    }
+    return __syncthreads_or(bad) == 0;
 }
 
 template <typename T, int NB, bool MIXED>
@@ -246,7 +474,8 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
         if (leaf < 0) break;
         LeafInfo L = leaf_info(P, leaf);
         L.flags = leaf_flags(L);
-        assemble<T>(M, L, P.kappa2);
+        const T *Dw = (const T *)(sizeof(T) == 4 ? (const void *)P.dt.dmat32 : (const void *)P.dt.dmat) + P.dt.doff[L.p];
+        assemble<T>(M, L, Dw, P.kappa2);
         __syncthreads();
         if constexpr (!MIXED) {
             lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, true, nullptr, ldp, sm);
@@ -256,36 +485,33 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
         } else {
             const long long mbytes = (((long long)L.n * L.LDC * (long long)sizeof(T)) + 255) & ~255LL;
             double *X = (double *)(slot + mbytes);
-            int *piv_g = (int *)(X + (long long)L.n * L.r);
-            lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, true, piv_g, ldp, sm);
-            for (long long e = threadIdx.x; e < (long long)L.n * L.r; e += NT) {
-                const int i = (int)(e / L.r), c = (int)(e % L.r);
-                X[e] = (double)M[(long long)i * L.LDC + L.n4 + c];
-            }
+            int *perm_g = (int *)(X + (long long)L.n * L.r);   // 3 NB ints per panel
+            lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm);
+            float *eta = (float *)(perm_g + 3 * (L.n + 64));
+            float *nf = eta + ((L.r + 63) & ~63);                 // 12 floats per interior node
+            const float *Dhi = P.dt.dmat32 + P.dt.doff[L.p], *Dlo = P.dt.dmat_lo + P.dt.doff[L.p];
+            node_factors(L, P.kappa2, nf);
+            // residual column chunk: as many FP64 columns as the panel and
+            // chunk buffers hold (they are idle between eliminations)
+            // the D/D^2 pairs take the front of the buffer, X chunks the rest
+            const int dpairs = 2 * L.p * L.p;
+            const int xs_cap = (int)(((size_t)NB * (ldp + Cfg<T, NB>::CH) * sizeof(T) / sizeof(float2) - dpairs) / L.n);
+            const int xs_cols = xs_cap >= 16 ? 16 : xs_cap >= 8 ? 8 : 4;
+            for (int i = threadIdx.x >> 5; i < L.n; i += NWARP)
+                for (int c = threadIdx.x & 31; c < L.r; c += 32)
+                    X[(long long)i * L.r + c] = f2d((float)M[(long long)i * L.LDC + L.n4 + c]);
+            for (int c = threadIdx.x; c < L.r; c += NT) eta[c] = 1.0f;
             __syncthreads();
             int status = sm.misc[1];
             if (status == 0 && P.kmax > 0) {
                 int it = 0;
                 bool done = false;
                 while (!done && it < P.kmax) {
-                    residual<T>(M, X, L, P.kappa2);
+                    residual<T>(M, X, L, Dhi, Dlo, nf, (float2 *)sm.Ps + 2 * L.p * L.p, (float2 *)sm.Ps, xs_cols);
                     __syncthreads();
-                    lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, false, piv_g, ldp, sm);
-                    int bad = 0;
-                    for (int c = threadIdx.x; c < L.r; c += NT) {
-                        double dmax = 0.0, xmax = 0.0;
-                        for (int i = 0; i < L.n; ++i) {
-                            const double d = (double)M[(long long)i * L.LDC + L.n4 + c];
-                            const double x = X[(long long)i * L.r + c] + d;
-                            X[(long long)i * L.r + c] = x;
-                            dmax = fmax(dmax, fabs(d));
-                            xmax = fmax(xmax, fabs(x));
-                        }
-                        if (!(dmax <= P.tol * xmax)) bad = 1;
-                    }
-                    bad = __syncthreads_or(bad);
+                    lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
+                    done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us);
                     ++it;
-                    done = !bad;
                 }
                 if (!done) status = -it;
             }
@@ -356,18 +582,26 @@ cudaError_t launch_one(const CondenseParams &prm, int grid, cudaStream_t s) {
 }  // namespace
 
 // Panel width: the widest whose shared memory still allows three CTAs per
-// SM (75 KB), never below 4.
-LuBlocking choose_blocking(int prec, int nmax) {
+// SM (75 KB), never below 4.  The mixed path also stages, between
+// eliminations, the differentiation pairs and 4 columns of the FP64 iterate
+// in the panel and chunk buffers; the panel is widened until they fit.
+LuBlocking choose_blocking(int prec, int nmax, int pmax) {
     LuBlocking b;
     b.ldp = panel_ld(nmax);
     const bool dbl = prec == HPS_FP64;
     const int cands[3] = {dbl ? 16 : 32, dbl ? 8 : 16, dbl ? 4 : 8};
-    b.nb_panel = cands[2];
-    for (int nb : cands) {
-        const size_t s = dbl ? (nb == 16 ? smem_of<double, 16>(b.ldp) : nb == 8 ? smem_of<double, 8>(b.ldp) : smem_of<double, 4>(b.ldp))
-                             : (nb == 32 ? smem_of<float, 32>(b.ldp) : nb == 16 ? smem_of<float, 16>(b.ldp) : smem_of<float, 8>(b.ldp));
-        if (s <= 75 * 1024) { b.nb_panel = nb; break; }
+    auto bytes = [&](int nb) {
+        return dbl ? (nb == 16 ? smem_of<double, 16>(b.ldp) : nb == 8 ? smem_of<double, 8>(b.ldp) : smem_of<double, 4>(b.ldp))
+                   : (nb == 32 ? smem_of<float, 32>(b.ldp) : nb == 16 ? smem_of<float, 16>(b.ldp) : smem_of<float, 8>(b.ldp));
+    };
+    int pick = 2;
+    for (int t = 0; t < 3; ++t)
+        if (bytes(cands[t]) <= 75 * 1024) { pick = t; break; }
+    if (!dbl) {
+        const size_t need = (size_t)(2 * pmax * pmax + 4 * nmax) * 8;
+        while (pick > 0 && (size_t)cands[pick] * (b.ldp + 64) * sizeof(float) < need) --pick;
     }
+    b.nb_panel = cands[pick];
     return b;
 }
 

@@ -15,8 +15,8 @@
 // Then U X = Y is solved in place for the right-hand columns by block rows
 // from the bottom with the same chunk / tile machinery.
 //
-// With factor = false the stored factors and pivots are replayed on the
-// right-hand columns only (used by iterative refinement).
+// With factor = false the stored factors and panel permutations are
+// replayed on the right-hand columns only (used by iterative refinement).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -48,7 +48,7 @@ template <typename T>
 struct Smem {
     T *Ps;     // NB x ldp, panel (column-major)
     T *Us;     // NB x CH, current row block of the right part
-    T *redv;   // NWARP
+    T *redv;   // NB + 8 + NWARP: argmax partials, sub-panel pivot row, diagonal reciprocals
     int *redi; // NWARP
     int *piv;  // NB: panel-relative pivot rows
     int *xsrc; // NB: source of displaced row j (or -1)
@@ -59,7 +59,7 @@ struct Smem {
 
 template <typename T, int NB>
 __host__ __device__ constexpr size_t smem_bytes_for(int ldp) {
-    return sizeof(T) * ((size_t)NB * ldp + (size_t)NB * Cfg<T, NB>::CH + 2 * NWARP) +
+    return sizeof(T) * ((size_t)NB * ldp + (size_t)NB * Cfg<T, NB>::CH + NB + 8 + NWARP) +
            sizeof(int) * (NWARP + 3 * NB + 16 + ldp) + 64;
 }
 
@@ -72,7 +72,7 @@ __device__ Smem<T> carve(unsigned char *base, int ldp) {
     s.Us = t;
     t += (size_t)NB * Cfg<T, NB>::CH;
     s.redv = t;
-    t += 2 * NWARP;
+    t += NB + 8 + NWARP;
     int *ip = (int *)t;
     s.redi = ip;
     ip += NWARP;
@@ -91,6 +91,23 @@ __device__ Smem<T> carve(unsigned char *base, int ldp) {
 template <typename T>
 __device__ __forceinline__ T absval(T v) { return v < T(0) ? -v : v; }
 
+// Asynchronous global -> shared copies (cp.async): every thread issues its
+// copies without waiting on each load; cp_async_wait() then waits for this
+// thread's copies, and a __syncthreads() publishes them to the CTA.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *s, const void *g) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(g), "n"(BYTES) : "memory");
+    }
+}
+
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Copy rows [0, rows) x columns [0, cols) of a row-major global block (ld
 // LDC) to / from a column-major shared block (ld ldp).  Each warp touches
 // whole 32-byte sectors of RW rows; with ldp = 4 (mod 32) the shared-memory
@@ -107,81 +124,245 @@ __device__ __forceinline__ void stage(T *__restrict__ g, int LDC, T *__restrict_
         for (int rg = warp * RW; rg < rows; rg += NWARP * RW) {
             const int rr = rg + rin;
             if (rr >= rows) continue;
-            if (TO_SHARED) s[cc * ldp + rr] = g[(long long)rr * LDC + cc];
+            if (TO_SHARED) cp_async<sizeof(T)>(&s[cc * ldp + rr], &g[(long long)rr * LDC + cc]);
             else g[(long long)rr * LDC + cc] = s[cc * ldp + rr];
         }
     }
+    if (TO_SHARED) cp_async_wait();
 }
 
-// Factor the shared-memory panel P (mp rows, nbk columns, ld ldp).
+// Sub-panel width and the most panel rows a thread holds in registers.
+template <typename T> struct PanelCfg;
+template <> struct PanelCfg<float> { static constexpr int W = 8, RMAX = 8; };
+template <> struct PanelCfg<double> { static constexpr int W = 8, RMAX = 4; };
+
+// Argmax of |value| over the CTA: (best, row) partials per thread -> the
+// row index every thread agrees on (largest magnitude, first row on ties).
 template <typename T>
+__device__ __forceinline__ int block_argmax(T best, int bi, const Smem<T> &sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { sm.redv[warp] = best; sm.redi[warp] = bi; }
+    __syncthreads();
+    best = sm.redv[0];
+    bi = sm.redi[0];
+#pragma unroll
+    for (int w = 1; w < NWARP; ++w) {
+        const T ov = sm.redv[w];
+        const int oi = sm.redi[w];
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    return bi;
+}
+
+// Record pivot j -> pr (thread 0) in piv and the row map.
+template <typename T>
+__device__ __forceinline__ void record_pivot(int j, int pr, const Smem<T> &sm) {
+    if (threadIdx.x == 0) {
+        sm.piv[j] = pr;
+        const int t = sm.map[j];
+        sm.map[j] = sm.map[pr];
+        sm.map[pr] = t;
+    }
+}
+
+// Factor the shared-memory panel P (mp rows, nbk columns, ld ldp) with
+// partial pivoting.  Also tracks the net row permutation in sm.map
+// (panel-relative: row j of the factored panel is original row map[j]);
+// sm.map must hold the identity on entry.  The first exact zero pivot sets
+// sm.misc[1] (1-based, offset k0) and leaves its column unscaled.
+//
+// Sub-panels of W columns are factored with each thread holding its rows
+// of the sub-panel in registers (rank-1 updates are register FMAs; row
+// interchanges go through a small shared buffer); the rest of the panel is
+// then updated as a block with the sub-panel's L still in registers.
+// Panels taller than RMAX * NT rows use the shared-memory form throughout.
+template <typename T, int NB>
 __device__ void panel_factor(T *__restrict__ P, int ldp, int mp, int nbk, int k0, const Smem<T> &sm) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j = 0; j < nbk; ++j) {
-        T best = T(-1);
-        int bi = 0x7fffffff;
-        for (int i = j + tid; i < mp; i += NT) {
-            const T v = absval(P[j * ldp + i]);
-            if (v > best) { best = v; bi = i; }
+    constexpr int W = PanelCfg<T>::W, RMAX = PanelCfg<T>::RMAX;
+    using V = typename Vec<T>::type;
+    constexpr int HV = Vec<T>::N;
+    const int tid = threadIdx.x;
+    if (mp > RMAX * NT) {
+        for (int j = 0; j < nbk; ++j) {
+            T best = T(-1);
+            int bi = 0x7fffffff;
+            for (int i = j + tid; i < mp; i += NT) {
+                const T v = absval(P[j * ldp + i]);
+                if (v > best) { best = v; bi = i; }
+            }
+            bi = block_argmax<T>(best, bi, sm);
+            const int pr = (bi >= mp || bi < j) ? j : bi;
+            record_pivot<T>(j, pr, sm);
+            if (pr != j) {
+                for (int c = tid; c < nbk; c += NT) {
+                    const T a = P[c * ldp + j];
+                    P[c * ldp + j] = P[c * ldp + pr];
+                    P[c * ldp + pr] = a;
+                }
+            }
+            __syncthreads();
+            const T pv = P[j * ldp + j];
+            if (pv == T(0)) {
+                if (tid == 0 && sm.misc[1] == 0) sm.misc[1] = k0 + j + 1;
+            } else {
+                const T inv = T(1) / pv;
+                for (int i = j + 1 + tid; i < mp; i += NT) {
+                    const T l = P[j * ldp + i] * inv;
+                    P[j * ldp + i] = l;
+#pragma unroll
+                    for (int c = 1; c < NB; ++c)
+                        if (c > j && c < nbk) P[c * ldp + i] = fma(-l, P[c * ldp + j], P[c * ldp + i]);
+                }
+            }
+            __syncthreads();
+        }
+        return;
+    }
+    T *bufA = sm.redv + NWARP;   // pivot row of the sub-panel (W values)
+    T *bufB = sm.Us;             // displaced row (W values); Us is idle here
+    for (int s0 = 0; s0 < nbk; s0 += W) {
+        const int w = min(W, nbk - s0);
+        // rows i = s0 + tid + t * NT of columns s0 .. s0 + w - 1 into registers
+        T a[RMAX][W];
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+            const int i = s0 + tid + t * NT;
+#pragma unroll
+            for (int c = 0; c < W; ++c) a[t][c] = (i < mp && c < w) ? P[(s0 + c) * ldp + i] : T(0);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) { sm.redv[warp] = best; sm.redi[warp] = bi; }
-        __syncthreads();
-        best = sm.redv[0];
-        bi = sm.redi[0];
+        for (int jj = 0; jj < W; ++jj) {
+            if (jj < w) {
+                const int j = s0 + jj;
+                T best = T(-1);
+                int bi = 0x7fffffff;
 #pragma unroll
-        for (int w = 1; w < NWARP; ++w) {
-            const T ov = sm.redv[w];
-            const int oi = sm.redi[w];
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        const int pr = (bi >= mp || bi < j) ? j : bi;   // no finite candidate: keep the row
-        if (tid == 0) sm.piv[j] = pr;
-        if (pr != j) {
-            for (int c = tid; c < nbk; c += NT) {
-                const T a = P[c * ldp + j];
-                P[c * ldp + j] = P[c * ldp + pr];
-                P[c * ldp + pr] = a;
+                for (int t = 0; t < RMAX; ++t) {
+                    const int i = s0 + tid + t * NT;
+                    const T v = absval(a[t][jj]);
+                    if (i >= j && i < mp && v > best) { best = v; bi = i; }
+                }
+                bi = block_argmax<T>(best, bi, sm);
+                const int pr = (bi >= mp || bi < j) ? j : bi;
+                record_pivot<T>(j, pr, sm);
+                // owners: row x belongs to thread (x - s0) % NT, slot (x - s0) / NT
+                const int oj = (j - s0) % NT, sj = (j - s0) / NT;
+                const int op = (pr - s0) % NT, sp = (pr - s0) / NT;
+#pragma unroll
+                for (int t = 0; t < RMAX; ++t) {
+                    if (tid == op && t == sp)
+#pragma unroll
+                        for (int c = 0; c < W; ++c) bufA[c] = a[t][c];
+                    if (pr != j && tid == oj && t == sj)
+#pragma unroll
+                        for (int c = 0; c < W; ++c) bufB[c] = a[t][c];
+                }
+                if (pr != j) {   // the panel columns outside the sub-panel
+                    for (int c = tid; c < nbk; c += NT) {
+                        if (c >= s0 && c < s0 + w) continue;
+                        const T x = P[c * ldp + j];
+                        P[c * ldp + j] = P[c * ldp + pr];
+                        P[c * ldp + pr] = x;
+                    }
+                }
+                __syncthreads();
+                T prow[W];
+#pragma unroll
+                for (int c = 0; c < W; ++c) prow[c] = bufA[c];
+                if (pr != j) {
+#pragma unroll
+                    for (int t = 0; t < RMAX; ++t) {
+                        if (tid == oj && t == sj)
+#pragma unroll
+                            for (int c = 0; c < W; ++c) a[t][c] = prow[c];
+                        if (tid == op && t == sp)
+#pragma unroll
+                            for (int c = 0; c < W; ++c) a[t][c] = bufB[c];
+                    }
+                }
+                const T pv = prow[jj];
+                if (pv == T(0)) {
+                    if (tid == 0 && sm.misc[1] == 0) sm.misc[1] = k0 + j + 1;
+                } else {
+                    const T inv = T(1) / pv;
+#pragma unroll
+                    for (int t = 0; t < RMAX; ++t) {
+                        const int i = s0 + tid + t * NT;
+                        if (i > j && i < mp) {
+                            const T l = a[t][jj] * inv;
+                            a[t][jj] = l;
+#pragma unroll
+                            for (int c = jj + 1; c < W; ++c) a[t][c] = fma(-l, prow[c], a[t][c]);
+                        }
+                    }
+                }
             }
         }
-        __syncthreads();
-        const T pv = P[j * ldp + j];
-        if (pv == T(0)) {
-            if (tid == 0 && sm.misc[1] == 0) sm.misc[1] = k0 + j + 1;
-        } else {
-            const T inv = T(1) / pv;
-            for (int i = j + 1 + tid; i < mp; i += NT) {
-                const T l = P[j * ldp + i] * inv;
-                P[j * ldp + i] = l;
-                for (int c = j + 1; c < nbk; ++c) P[c * ldp + i] = fma(-l, P[c * ldp + j], P[c * ldp + i]);
-            }
+        // sub-panel back to shared memory
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) {
+            const int i = s0 + tid + t * NT;
+            if (i < mp)
+#pragma unroll
+                for (int c = 0; c < W; ++c)
+                    if (c < w) P[(s0 + c) * ldp + i] = a[t][c];
         }
         __syncthreads();
+        if (s0 + w < nbk) {
+            // top rows of the remaining columns: U = L11^{-1} A (unit lower)
+            for (int c = s0 + w + tid; c < nbk; c += NT) {
+                T u[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) u[k] = P[c * ldp + s0 + k];
+#pragma unroll
+                for (int k = 0; k < W; ++k)
+#pragma unroll
+                    for (int i2 = k + 1; i2 < W; ++i2) u[i2] = fma(-P[(s0 + k) * ldp + s0 + i2], u[k], u[i2]);
+#pragma unroll
+                for (int k = 0; k < W; ++k) P[c * ldp + s0 + k] = u[k];
+            }
+            __syncthreads();
+            // rows below: A -= L (registers) * U (shared, 16-byte loads)
+            for (int c = s0 + w; c < nbk; ++c) {
+                T u[W];
+#pragma unroll
+                for (int g = 0; g < W / HV; ++g) {
+                    const V uv = *(const V *)(P + c * ldp + s0 + g * HV);
+                    const T *pu = (const T *)&uv;
+#pragma unroll
+                    for (int t = 0; t < HV; ++t) u[g * HV + t] = pu[t];
+                }
+#pragma unroll
+                for (int t = 0; t < RMAX; ++t) {
+                    const int i = s0 + tid + t * NT;
+                    if (i >= s0 + w && i < mp) {
+                        T v = P[c * ldp + i];
+#pragma unroll
+                        for (int k = 0; k < W; ++k) v = fma(-a[t][k], u[k], v);
+                        P[c * ldp + i] = v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 
-// Net row permutation of the panel's interchanges (panel-relative rows):
-// top row j receives source map[j]; displaced rows below the panel receive
-// xsrc[j] at xdst[j] (xdst = -1 when nothing lands there from step j).
+// Net row permutation of the panel's interchanges (panel-relative rows),
+// from the pivots and the map left by panel_factor: top row j receives
+// source map[j]; displaced rows below the panel receive xsrc[j] at xdst[j]
+// (xdst = -1 when nothing lands there from step j).  The sources of
+// displaced rows are always top rows, so gathering every source before any
+// store is race-free.
 template <typename T>
-__device__ void panel_permutation(int mp, int nbk, const Smem<T> &sm) {
+__device__ void panel_permutation(int nbk, const Smem<T> &sm) {
     const int tid = threadIdx.x;
-    for (int r = tid; r < mp; r += NT) sm.map[r] = r;
-    __syncthreads();
-    if (tid == 0) {
-        for (int j = 0; j < nbk; ++j) {
-            const int p = sm.piv[j];
-            const int t = sm.map[j];
-            sm.map[j] = sm.map[p];
-            sm.map[p] = t;
-        }
-    }
-    __syncthreads();
     for (int j = tid; j < nbk; j += NT) {
         const int p = sm.piv[j];
         bool last = p >= nbk;
@@ -232,9 +413,22 @@ __device__ __forceinline__ void gemm_sub(T *__restrict__ Mg, int LDC, int r0, in
                 }
             }
         }
+        // C -= acc, one half of the rows at a time: the half's 2HV vector
+        // loads are all issued before the first subtraction
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const int s = half ? sb : sa;
+            V cv[HV][2];
+#pragma unroll
+            for (int u = 0; u < HV; ++u) {
+                const int r = min(s + u, r1 - 1);
+                const T *row = Mg + (long long)r * LDC + c0;
+#pragma unroll
+                for (int hc = 0; hc < 2; ++hc) {
+                    const int c = hc ? cB : cA;
+                    cv[u][hc] = *(const V *)(row + (c < cw ? c : 0));   // clamped: stays in the row
+                }
+            }
 #pragma unroll
             for (int u = 0; u < HV; ++u) {
                 const int r = s + u;
@@ -244,11 +438,10 @@ __device__ __forceinline__ void gemm_sub(T *__restrict__ Mg, int LDC, int r0, in
                 for (int hc = 0; hc < 2; ++hc) {
                     const int c = hc ? cB : cA;
                     if (c >= cw) continue;
-                    V cv = *(V *)(row + c);
-                    T *pc = (T *)&cv;
+                    T *pc = (T *)&cv[u][hc];
 #pragma unroll
                     for (int v = 0; v < HV; ++v) pc[v] -= acc[half * HV + u][hc * HV + v];
-                    *(V *)(row + c) = cv;
+                    *(V *)(row + c) = cv[u][hc];
                 }
             }
         }
@@ -261,15 +454,19 @@ template <typename T, int NB>
 __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, int nbk, int cstart, int ldp,
                             const Smem<T> &sm) {
     using CF = Cfg<T, NB>;
-    constexpr int CH = CF::CH;
+    using V = typename Vec<T>::type;
+    constexpr int CH = CF::CH, HV = CF::HV;
     constexpr int XPT = (NB * CH + NT - 1) / NT;  // displaced-row elements per thread
     const int tid = threadIdx.x;
     for (int c0 = cstart; c0 < C; c0 += CH) {
         const int cw = min(CH, C - c0);
-        // gather: top rows into Us, displaced rows into registers
-        for (int e = tid; e < nbk * CH; e += NT) {
-            const int j = e / CH, c = e % CH;
-            if (c < cw) sm.Us[j * CH + c] = M[(long long)(k0 + sm.map[j]) * LDC + c0 + c];
+        // gather: top rows into Us (16-byte asynchronous copies; a vector
+        // starting before cw ends inside the padded row), displaced rows
+        // into registers
+        constexpr int VPR = CH / HV;
+        for (int e = tid; e < nbk * VPR; e += NT) {
+            const int j = e / VPR, c = (e % VPR) * HV;
+            if (c < cw) cp_async<16>(&sm.Us[j * CH + c], &M[(long long)(k0 + sm.map[j]) * LDC + c0 + c]);
         }
         T xv[XPT];
 #pragma unroll
@@ -279,6 +476,7 @@ __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, in
             xv[t] = T(0);
             if (e < nbk * CH && c < cw && sm.xsrc[j] >= 0) xv[t] = M[(long long)(k0 + sm.xsrc[j]) * LDC + c0 + c];
         }
+        cp_async_wait();
         __syncthreads();
 #pragma unroll
         for (int t = 0; t < XPT; ++t) {
@@ -286,18 +484,26 @@ __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, in
             const int j = e / CH, c = e % CH;
             if (e < nbk * CH && c < cw && sm.xdst[j] >= 0) M[(long long)(k0 + sm.xdst[j]) * LDC + c0 + c] = xv[t];
         }
-        // unit-lower solve, one column per thread, column in registers
+        // unit-lower solve, one column per thread, column in registers;
+        // column-oriented (axpy) so each step's multipliers L[j+1.., j] are
+        // consecutive in the shared panel and load as 16-byte vectors
         for (int c = tid; c < cw; c += NT) {
             T u[NB];
 #pragma unroll
             for (int j = 0; j < NB; ++j) u[j] = j < nbk ? sm.Us[j * CH + c] : T(0);
 #pragma unroll
-            for (int j = 1; j < NB; ++j) {
+            for (int j = 0; j < NB - 1; ++j) {
                 if (j < nbk) {
-                    T v = u[j];
+                    const T uj = u[j];
+                    const T *col = sm.Ps + j * ldp;
 #pragma unroll
-                    for (int i = 0; i < j; ++i) v = fma(-sm.Ps[i * ldp + j], u[i], v);
-                    u[j] = v;
+                    for (int g = (j + 1) / HV; g < NB / HV; ++g) {
+                        const V lv = *(const V *)(col + g * HV);
+                        const T *pl = (const T *)&lv;
+#pragma unroll
+                        for (int t = 0; t < HV; ++t)
+                            if (g * HV + t > j) u[g * HV + t] = fma(-pl[t], uj, u[g * HV + t]);
+                    }
                 }
             }
 #pragma unroll
@@ -315,26 +521,41 @@ __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, in
 }
 
 // Elimination on M = [A (n cols) | pad | RHS from column n4], C columns in
-// all, row-major with ld LDC (multiple of 4; M 16-byte aligned).
+// all, row-major with ld LDC (multiple of 4; M 16-byte aligned).  When
+// perm_g is given, factoring stores each panel's permutation there (3 NB
+// ints per panel: top-row sources, displaced sources, displaced targets)
+// and replaying (factor = false) reads it back.
 template <typename T, int NB>
-__device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool factor, int *piv_g, int ldp,
+__device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool factor, int *perm_g, int ldp,
                          const Smem<T> &sm) {
     using CF = Cfg<T, NB>;
-    constexpr int CH = CF::CH;
+    using V = typename Vec<T>::type;
+    constexpr int CH = CF::CH, HV = CF::HV;
     const int tid = threadIdx.x;
     for (int k0 = 0; k0 < n; k0 += NB) {
         const int nbk = min(NB, n - k0), mp = n - k0;
+        int *pg = perm_g ? perm_g + 3 * k0 : nullptr;
+        if (factor)
+            for (int r = tid; r < mp; r += NT) sm.map[r] = r;
+        else
+            for (int j = tid; j < nbk; j += NT) {
+                sm.map[j] = pg[j];
+                sm.xsrc[j] = pg[NB + j];
+                sm.xdst[j] = pg[2 * NB + j];
+            }
         stage<T, true>(M + (long long)k0 * LDC + k0, LDC, sm.Ps, ldp, mp, nbk);
-        if (!factor)
-            for (int j = tid; j < nbk; j += NT) sm.piv[j] = piv_g[k0 + j] - k0;
         __syncthreads();
         if (factor) {
-            panel_factor<T>(sm.Ps, ldp, mp, nbk, k0, sm);
+            panel_factor<T, NB>(sm.Ps, ldp, mp, nbk, k0, sm);
             stage<T, false>(M + (long long)k0 * LDC + k0, LDC, sm.Ps, ldp, mp, nbk);
-            if (piv_g)
-                for (int j = tid; j < nbk; j += NT) piv_g[k0 + j] = k0 + sm.piv[j];
+            panel_permutation<T>(nbk, sm);
+            if (pg)
+                for (int j = tid; j < nbk; j += NT) {
+                    pg[j] = sm.map[j];
+                    pg[NB + j] = sm.xsrc[j];
+                    pg[2 * NB + j] = sm.xdst[j];
+                }
         }
-        panel_permutation<T>(mp, nbk, sm);
         const int cstart = factor ? (k0 + nbk < n ? k0 + nbk : n4) : n4;
         apply_panel<T, NB>(M, LDC, n, C, k0, nbk, cstart, ldp, sm);
     }
@@ -344,20 +565,30 @@ __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool 
         const int nbk = min(NB, n - kb0), rows = kb0 + nbk;
         stage<T, true>(M + kb0, LDC, sm.Ps, ldp, rows, nbk);
         __syncthreads();
+        for (int j = tid; j < nbk; j += NT) sm.redv[j] = T(1) / sm.Ps[j * ldp + kb0 + j];
+        __syncthreads();
         for (int c0 = n4; c0 < C; c0 += CH) {
             const int cw = min(CH, C - c0);
             for (int c = tid; c < cw; c += NT) {
                 T u[NB];
 #pragma unroll
                 for (int j = 0; j < NB; ++j) u[j] = j < nbk ? M[(long long)(kb0 + j) * LDC + c0 + c] : T(0);
+                // column-oriented: u[i] /= U[i][i], then u[j] -= U[j][i] u[i]
+                // for j < i, with U[0..i)[i] consecutive in the shared block
 #pragma unroll
-                for (int j = NB - 1; j >= 0; --j) {
-                    if (j < nbk) {
-                        T v = u[j];
+                for (int i = NB - 1; i >= 0; --i) {
+                    if (i < nbk) {
+                        const T *col = sm.Ps + i * ldp + kb0;
+                        const T ui = u[i] * sm.redv[i];
+                        u[i] = ui;
 #pragma unroll
-                        for (int i = j + 1; i < NB; ++i)
-                            if (i < nbk) v = fma(-sm.Ps[i * ldp + kb0 + j], u[i], v);
-                        u[j] = v / sm.Ps[j * ldp + kb0 + j];
+                        for (int g = 0; g < (i + HV - 1) / HV; ++g) {
+                            const V uv = *(const V *)(col + g * HV);
+                            const T *pu = (const T *)&uv;
+#pragma unroll
+                            for (int t = 0; t < HV; ++t)
+                                if (g * HV + t < i) u[g * HV + t] = fma(-pu[t], ui, u[g * HV + t]);
+                        }
                     }
                 }
 #pragma unroll

@@ -84,6 +84,7 @@ struct hps_plan {
     DevBuf tables, work;
     int *d_p = nullptr, *d_order = nullptr, *d_doff = nullptr, *d_queue = nullptr;
     double *d_box = nullptr, *d_dmat = nullptr;
+    float *d_dmat32 = nullptr, *d_dmat_lo = nullptr;
     long long *d_off = nullptr;  // o_p2, o_ni, o_nb, o_sb, o_bb back to back
     int device = 0, sms = 0;
     bool timing = false;
@@ -215,7 +216,10 @@ hps_status hps_build_leaves(const hps_leaf_desc *desc, hps_plan **out, hps_strea
     const size_t sz_doff = round_up(sizeof(int) * (HPS_PMAX + 1), 256);
     const size_t sz_dmat = round_up(sizeof(double) * std::max<size_t>(dmat.size(), 1), 256);
     const size_t sz_q = 256;
-    err = P->tables.ensure(sz_p + sz_box + sz_off + sz_ord + sz_doff + sz_dmat + sz_q);
+    const size_t sz_dmat32 = round_up(sizeof(float) * std::max<size_t>(dmat.size(), 1), 256);
+    std::vector<float> dmat32(dmat.begin(), dmat.end()), dmat_lo(dmat.size());
+    for (size_t k = 0; k < dmat.size(); ++k) dmat_lo[k] = (float)(dmat[k] - (double)dmat32[k]);
+    err = P->tables.ensure(sz_p + sz_box + sz_off + sz_ord + sz_doff + sz_dmat + 2 * sz_dmat32 + sz_q);
     if (err != cudaSuccess) {
         g_build_error = std::string("hps_build_leaves: cudaMalloc: ") + cudaGetErrorString(err);
         delete P;
@@ -228,6 +232,8 @@ hps_status hps_build_leaves(const hps_leaf_desc *desc, hps_plan **out, hps_strea
     P->d_order = (int *)base; base += sz_ord;
     P->d_doff = (int *)base; base += sz_doff;
     P->d_dmat = (double *)base; base += sz_dmat;
+    P->d_dmat32 = (float *)base; base += sz_dmat32;
+    P->d_dmat_lo = (float *)base; base += sz_dmat32;
     P->d_queue = (int *)base;
     std::vector<long long> off;
     off.reserve(5LL * nl);
@@ -240,6 +246,10 @@ hps_status hps_build_leaves(const hps_leaf_desc *desc, hps_plan **out, hps_strea
     if (err == cudaSuccess) err = cudaMemcpyAsync(P->d_doff, doff.data(), sizeof(int) * doff.size(), cudaMemcpyHostToDevice, s);
     if (err == cudaSuccess && !dmat.empty())
         err = cudaMemcpyAsync(P->d_dmat, dmat.data(), sizeof(double) * dmat.size(), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess && !dmat32.empty())
+        err = cudaMemcpyAsync(P->d_dmat32, dmat32.data(), sizeof(float) * dmat32.size(), cudaMemcpyHostToDevice, s);
+    if (err == cudaSuccess && !dmat_lo.empty())
+        err = cudaMemcpyAsync(P->d_dmat_lo, dmat_lo.data(), sizeof(float) * dmat_lo.size(), cudaMemcpyHostToDevice, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);  // host staging vectors die here
     if (err != cudaSuccess) {
         g_build_error = std::string("hps_build_leaves: upload: ") + cudaGetErrorString(err);
@@ -271,9 +281,11 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     if (prec != HPS_FP64 && (kmax < 0 || !(tol >= 0.0)))
         return P->fail(HPS_ERR_ARG, "hps_condense: kmax < 0 or tol < 0");
     const bool mixed = prec != HPS_FP64;
+    if (mixed && 4 * (P->pmax - 2) + m > 256)
+        return P->fail(HPS_ERR_ARG, "hps_condense: mixed precision needs 4(p-2) + m <= 256");
     const size_t tsize = mixed ? sizeof(float) : sizeof(double);
     const int qmax = P->pmax - 2, nmax = qmax * qmax;
-    const LuBlocking blk = choose_blocking(prec, nmax);
+    const LuBlocking blk = choose_blocking(prec, nmax, P->pmax);
     const int per_sm = condense_max_ctas_per_sm(prec, blk);
     if (per_sm < 1) return P->fail(HPS_ERR_CUDA, "hps_condense: kernel does not fit on an SM");
     const int grid = std::min(P->n_leaves, P->sms * per_sm);
@@ -281,7 +293,7 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     for (int p = P->pmin; p <= P->pmax; ++p) {
         const long long q = p - 2, n = q * q, r = 4 * q + m, C = round_up(n, 4) + r, LDC = round_up(C, 4);
         long long b = n * LDC * (long long)tsize;
-        if (mixed) b = round_up(b, 256) + n * r * 8 + n * 4;
+        if (mixed) b = round_up(b, 256) + n * r * 8 + 3 * (n + 64) * 4 + round_up(r, 64) * 4 + n * 12 * 4;   // X, perms, eta, node factors
         slot = std::max(slot, round_up(b, 256));
     }
     cudaError_t e = P->work.ensure((size_t)slot * grid);
@@ -290,6 +302,8 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     prm.blk = blk;
     prm.lt = P->leaf_tables();
     prm.dt.dmat = P->d_dmat;
+    prm.dt.dmat32 = P->d_dmat32;
+    prm.dt.dmat_lo = P->d_dmat_lo;
     prm.dt.doff = P->d_doff;
     prm.n_leaves = P->n_leaves;
     prm.m = m;

@@ -26,6 +26,8 @@ struct LeafTables {
 // D of order p at dmat + doff[p], followed by D*D.
 struct DTables {
     const double *dmat;
+    const float *dmat32;  // the same tables rounded to FP32, same offsets
+    const float *dmat_lo; // dmat - dmat32 rounded to FP32 (double-float low parts)
     const int *doff;  // [HPS_PMAX + 1], -1 where absent
 };
 
@@ -55,7 +57,7 @@ struct CondenseParams {
 };
 
 // Host-side launchers (condense.cu).
-LuBlocking choose_blocking(int prec, int nmax);
+LuBlocking choose_blocking(int prec, int nmax, int pmax);
 size_t condense_smem(int prec, const LuBlocking &b);
 int condense_max_ctas_per_sm(int prec, const LuBlocking &b);
 cudaError_t launch_condense(int prec, const CondenseParams &prm, int grid, cudaStream_t s);
