@@ -149,6 +149,31 @@ hps_status hps_solve(hps_plan *plan, const double *d_g, const double *d_S, const
 hps_status hps_set_timing(hps_plan *plan, int enable);
 hps_status hps_phase_times(hps_plan *plan, float *ms, int n);
 
+/* FP64 condensation of a batch of leaves of one order p, with no device
+ * allocation at all.  There is no counterpart in the paper: this entry point
+ * serves callers that cannot call cudaMalloc when they condense -- code
+ * inside a host framework that owns all device memory through its own pool
+ * and forbids outside allocations, or a latency-critical loop where an
+ * allocation could block on device synchronisation or fail under memory
+ * pressure.  It computes exactly what hps_condense(HPS_FP64) computes for a
+ * plan of n_leaves leaves of order p (same layouts, same info codes).
+ * Inputs: d_box device [n_leaves][4] (x0, y0, hx, hy); d_coef, d_f, m as in
+ *         hps_condense.  Outputs: d_S (may be NULL), d_T, d_h, d_W, d_info.
+ * Scratch: the tables and elimination workspace live in a fixed 32 MiB
+ * device array inside the library, held by every GPU that loads the library
+ * until the process exits.  A call whose tables plus one leaf's workspace
+ * ((p-2)^2 x (round4((p-2)^2) + 4(p-2) + m) doubles) do not fit is rejected
+ * with HPS_ERR_ARG; a smaller fit means fewer leaves in flight.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls on a device share the array: calls that overlap on the GPU (on
+ * different streams, or from different host threads without ordering) race
+ * and corrupt each other's results.  Errors: HPS_ERR_ARG / HPS_ERR_CUDA, with
+ * the message in hps_last_error(NULL). */
+hps_status hps_condense_noalloc(int n_leaves, int p, double kappa, const double *d_box,
+                                const double *d_coef, const double *d_f, int m, double *d_S,
+                                double *d_T, double *d_h, double *d_W, int *d_info, hps_stream stream);
+
 /* Number of kernel launches enqueued by the last hps_condense call. */
 int hps_last_launch_count(const hps_plan *plan);
 

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhps.so")
-SOURCES = ["hps_api.cu", "condense.cu", "merge.cu"]
+SOURCES = ["hps_api.cu", "condense.cu", "merge.cu", "noalloc.cu"]
 HEADERS = ["hps_internal.cuh", "dense_lu.cuh", "merge.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -73,6 +73,11 @@ void chebyshev_matrix(int p, std::vector<double> &D) {
 
 }  // namespace
 
+namespace hps {
+// Sets the text returned by hps_last_error(NULL) (calls without a plan).
+void set_global_error(const std::string &msg) { g_build_error = msg; }
+}  // namespace hps
+
 struct hps_plan {
     int n_leaves = 0;
     double kappa = 0.0;
