@@ -35,6 +35,26 @@ METRIC = "leaf condensations/s and TFLOP/s, mixed vs FP64 GPU path at rel err â‰
 UNIT = "leaf condensations/s"
 
 
+# DRAM bytes per full 4096-leaf launch from the ncu capture summarised in
+# profiles/condense_kernel_bumps_p20.md (592-leaf case scaled by 4096/592),
+# keyed by the hash of the kernel sources it was taken on; reported only
+# while the sources still hash to that value.
+TRAFFIC_BY_SOURCE = {"37cade5d7af990b4": {"fp32": 40.77e9, "fp64": 73.83e9}}
+
+
+def source_hash():
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2211_14969_b300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu"))) + sorted(glob.glob(os.path.join(csrc, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "hps.h"))
+    h = hashlib.sha256()
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def leaf_flops(p):
     q = p - 2
     n, nb = q * q, 4 * q
@@ -309,6 +329,7 @@ def run_gpu(args, rank, ws):
 
     flops = n * leaf_flops(20)
     pk = peaks()
+    traffic = TRAFFIC_BY_SOURCE.get(source_hash(), {}) if n == 4096 else {}
     res = {}
     uuid = None
     try:
@@ -332,7 +353,9 @@ def run_gpu(args, rank, ws):
                      "tflops": ws * flops / (per_step * 1e-3) / 1e12, "kernel_ms": kernel_ms,
                      "info_nonzero": int((info != 0).sum()),
                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": achieved / peak, "traffic": None},
+                                  "frac": achieved / peak, "traffic": traffic.get(name),
+                                  "peak_source": "fp32: 148 SMs x 128 lanes x 2 x max SM clock (unit counts)"
+                                  if name == "fp32" else "fp64: nominal 1.25 TFLOP/s of the part"},
                      "clocks": cs.summary()}
     if args.prec != "both" or args.leaves:
         if rank == 0:
