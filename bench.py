@@ -55,10 +55,30 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def leaf_flops(p):
+def leaf_flops(p, m=0):
+    """Algorithmic flops of one leaf: LU of A_ii, the solves for the n_b
+    boundary columns and m loads, and the DtN rows (m = 0 gives the
+    per-leaf figure of the S/T operators alone)."""
     q = p - 2
     n, nb = q * q, 4 * q
-    return (2.0 / 3.0) * n ** 3 + 2.0 * n * n * nb + 2.0 * nb * nb * q
+    return (2.0 / 3.0) * n ** 3 + 2.0 * n * n * (nb + m) + 2.0 * nb * (nb + m) * q
+
+
+WORKLOADS = {
+    "bumps_p20": ("64x64 leaves (4096) of the unit square, p=20 (A_ii 324x324), kappa=200, "
+                  "b=1-0.5exp(-|x-c|^2/0.02), m=1 body load of 16 Gaussian bumps (seed 2)"),
+    "bumps_p30": "32x32 leaves (1024), p=30 (A_ii 784x784), kappa=200, b and loads as bumps_p20 (seed 3)",
+    "annulus_p24": ("annular sector r in [1,2], theta in [0,pi/2] mapped to the unit square, 64x128 leaves "
+                    "(8192), p=24, kappa=400, b=1-0.3sin(4r)cos(6theta), m=1 (seed 4)"),
+    "uneven": ("128x80 leaves (10240) of the unit square, p drawn from {12,16,20,24,32} with weights "
+               "{.3,.25,.2,.15,.1} (seed 5), kappa=300, b as bumps_p20, m=64 body loads"),
+}
+
+
+def make_workload(name):
+    from paper_2211_14969_b300 import workloads as WL
+    return {"bumps_p20": WL.bumps_p20, "bumps_p30": WL.bumps_p30, "annulus_p24": WL.annulus_p24,
+            "uneven": WL.uneven}[name]()
 
 
 def peaks():
@@ -174,22 +194,33 @@ class ClockSampler:
 # ---------------------------------------------------------------- workload
 
 def make_inputs(w, plan):
-    """Coefficients and body loads at the library's node coordinates (host)."""
+    """Coefficients and body loads at the library's node coordinates (host),
+    packed leaf after leaf; one vectorised evaluation per leaf order."""
     lay = plan.layout
     xy = plan.leaf_nodes().cpu().numpy()
-    p2 = int(lay.p2[0])
-    X = xy.reshape(w.n_leaves, 2, p2)
-    x, y = X[:, 0, :], X[:, 1, :]
-    coef = np.ascontiguousarray(np.moveaxis(w.coefficients(x, y), 0, 1))  # (n, 6, p2)
-    f = np.ascontiguousarray(w.body_load(x, y))                            # (n, p2, m)
-    return coef.ravel(), f.ravel()
+    coef = np.empty(int(6 * lay.o_p2[-1]))
+    f = np.empty(int(lay.o_p2[-1] * w.m))
+    p_all = np.asarray(lay.p)
+    for p in np.unique(p_all):
+        idx = np.flatnonzero(p_all == p)
+        p2 = int(p * p)
+        o = lay.o_p2[idx].astype(np.int64)
+        gx = (2 * o)[:, None] + np.arange(p2)[None, :]
+        x, y = xy[gx], xy[gx + p2]
+        c = np.moveaxis(w.coefficients(x, y), 0, 1)                       # (k, 6, p2)
+        coef[(6 * o)[:, None] + np.arange(6 * p2)[None, :]] = c.reshape(len(idx), -1)
+        fl = w.body_load(x, y).reshape(len(idx), -1)                       # (k, p2 * m)
+        f[(o * w.m)[:, None] + np.arange(p2 * w.m)[None, :]] = fl
+    return coef, f
 
 
-def rel_leafwise(a, b, n_leaves):
-    a = a.reshape(n_leaves, -1)
-    b = b.reshape(n_leaves, -1)
-    num = (a - b).norm(dim=1)
-    den = b.norm(dim=1).clamp_min(1e-300)
+def rel_leafwise(a, b, sizes):
+    """max over leaves of ||a_l - b_l|| / ||b_l|| for packed per-leaf blocks
+    of the given sizes."""
+    import torch
+    lengths = torch.as_tensor(np.asarray(sizes, dtype=np.int64), device=a.device)
+    num = torch.segment_reduce((a - b) ** 2, "sum", lengths=lengths).sqrt()
+    den = torch.segment_reduce(b * b, "sum", lengths=lengths).sqrt().clamp_min(1e-300)
     return float((num / den).max())
 
 
@@ -214,8 +245,9 @@ def time_steps(fn, steps, warmup, ws, stream, on_start=None):
     return max_over_ranks(ms, ws)
 
 
-def cpu_baseline(w, budget_s, gpu_out=None, sample_cap=None):
-    """The FP64 oracle as it stands, leaf by leaf, on a bounded sample."""
+def cpu_baseline(w, budget_s, sample_cap=None, seed=1234):
+    """The FP64 oracle as it stands, leaf by leaf, on a bounded random
+    sample of the workload's leaves (about budget_s seconds)."""
     import oracle.hps_oracle as O
     try:
         from threadpoolctl import threadpool_info
@@ -223,37 +255,39 @@ def cpu_baseline(w, budget_s, gpu_out=None, sample_cap=None):
     except Exception:
         cores = 1
     boxes = w.boxes()
-    p = int(w.p[0])
-    rng = np.random.default_rng(1234)
+    rng = np.random.default_rng(seed)
     order = rng.permutation(w.n_leaves)
     done, t0 = [], time.perf_counter()
     results = {}
     for l in order:
+        p = int(w.p[l])
         x, y = O.leaf_nodes(p, boxes[l])
-        out = O.condense_leaf(p, boxes[l], w.coefficients(x, y), w.kappa, w.body_load(x, y).reshape(p * p, -1))
-        results[int(l)] = out
+        f = w.body_load(x, y).reshape(p * p, -1) if w.m > 0 else None
+        results[int(l)] = O.condense_leaf(p, boxes[l], w.coefficients(x, y), w.kappa, f)
         done.append(int(l))
         if time.perf_counter() - t0 > budget_s or (sample_cap and len(done) >= sample_cap):
             break
     dt = time.perf_counter() - t0
     rec = {"value": len(done) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{len(done)} random leaves of the 4096 (p=20), {dt:.1f} s, numpy/LAPACK FP64 "
-                     f"(OpenBLAS threads {cores})"}
+           "sample": f"{len(done)} random leaves of the {w.n_leaves}, {dt:.1f} s, numpy/LAPACK FP64 "
+                     f"(BLAS threads {cores})"}
     return rec, results
 
 
 def parity_vs_oracle(w, lay, outs, results):
     """Max per-leaf relative error of GPU outputs against the oracle leaves."""
     worst = {}
+    m = w.m
     for name, out in outs.items():
         e = 0.0
         for l, ref in results.items():
             ni, nb = int(lay.ni[l]), int(lay.nb[l])
-            S = out["S"][int(lay.o_sb[l]):int(lay.o_sb[l + 1])].reshape(ni, nb)
-            T = out["T"][int(lay.o_bb[l]):int(lay.o_bb[l + 1])].reshape(nb, nb)
-            h = out["h"][int(lay.o_nb[l]):int(lay.o_nb[l + 1])].reshape(nb, 1)
-            W = out["W"][int(lay.o_ni[l]):int(lay.o_ni[l + 1])].reshape(ni, 1)
-            for a, b in ((S, ref["S"]), (T, ref["T"]), (h, ref["h"]), (W, ref["W"])):
+            pairs = [(out["S"][int(lay.o_sb[l]):int(lay.o_sb[l + 1])].reshape(ni, nb), ref["S"]),
+                     (out["T"][int(lay.o_bb[l]):int(lay.o_bb[l + 1])].reshape(nb, nb), ref["T"])]
+            if m > 0:
+                pairs.append((out["h"][int(lay.o_nb[l]) * m:int(lay.o_nb[l + 1]) * m].reshape(nb, m), ref["h"]))
+                pairs.append((out["W"][int(lay.o_ni[l]) * m:int(lay.o_ni[l + 1]) * m].reshape(ni, m), ref["W"]))
+            for a, b in pairs:
                 e = max(e, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
         worst[name] = e
     return worst
@@ -261,37 +295,38 @@ def parity_vs_oracle(w, lay, outs, results):
 
 # ---------------------------------------------------------------- arms
 
-def config_block(w, ws):
-    return {"workload": "bumps_p20: unit square, 64x64 leaves (4096), p=20 (A_ii 324x324), kappa=200, "
-                        "b=1-0.5exp(-|x-c|^2/0.02), m=1 body load of 16 Gaussian bumps (seed 2)",
-            "n_leaves_per_rank": w.n_leaves, "p": 20, "m": w.m,
+def config_block(name, w, ws, graph=False):
+    out_gb = (sum(int(p - 2) ** 2 * 4 * int(p - 2) + 16 * int(p - 2) ** 2 + int(p - 2) ** 2 * w.m
+                  + 4 * int(p - 2) * w.m for p in w.p) * 8) / 1e9
+    return {"workload": f"{name}: {WORKLOADS[name]}",
+            "n_leaves_per_rank": w.n_leaves, "p": sorted(set(int(v) for v in w.p)), "m": w.m,
             "parallelism": f"leaf-parallel, {ws} rank(s), no collective",
-            "l2": "no flush: per step the outputs alone are 0.95 GB (S 764 MB) > 126 MB L2"}
+            "launch": "CUDA graph replay of the persistent kernel" if graph else "one persistent kernel launch",
+            "l2": f"no flush: per step the outputs alone are {out_gb:.2f} GB > 126 MB L2"}
 
 
 def run_reference(args, rank, ws):
-    from paper_2211_14969_b300 import workloads as WL
+    """The reference arm: the FP64 CPU oracle, a bounded sample per step."""
     if rank != 0:
         return
-    w = WL.bumps_p20()
+    w = make_workload(args.workload)
     per_step = 16
-    # warmup
     for _ in range(args.warmup):
         cpu_baseline(w, 1e9, sample_cap=2)
     t0 = time.perf_counter()
-    n = 0
-    for _ in range(args.steps):
-        rec, _ = cpu_baseline(w, 1e9, sample_cap=per_step)
-        n += per_step
+    rec = None
+    for s in range(args.steps):
+        rec, _ = cpu_baseline(w, 1e9, sample_cap=per_step, seed=1234 + s)
     dt = time.perf_counter() - t0
-    value = n / dt
+    value = per_step * args.steps / dt
+    flops = float(np.mean([leaf_flops(int(p), w.m) for p in w.p]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(w, 1),
-            "tflops": value * leaf_flops(20) / 1e12,
+            "data": "synthetic", "config": config_block(args.workload, w, 1),
+            "tflops": value * flops / 1e12,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": rec["cores"], "kind": "oracle",
-                             "sample": f"{per_step} random leaves per step of the 4096 (p=20), FP64 numpy/LAPACK"},
+                             "sample": f"{per_step} random leaves per step of the {w.n_leaves}, FP64 numpy/LAPACK"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -301,14 +336,15 @@ def run_gpu(args, rank, ws):
     from paper_2211_14969_b300 import hps
     from paper_2211_14969_b300 import workloads as WL
 
-    w = WL.bumps_p20()
+    w = make_workload(args.workload)
     if args.leaves:
-        w = WL.scaled(w, 64, 64)
-        w.nx, w.ny = 1, args.leaves        # first N leaves of the 64 x 64 tiling
-        full_boxes = WL.bumps_p20().boxes()[: args.leaves]
+        full_boxes = w.boxes()[: args.leaves]
+        w = WL.scaled(w, w.nx, w.ny)
+        w.nx, w.ny = 1, args.leaves        # the first N leaves of the tiling
         w.boxes = lambda: full_boxes
         w.p = w.p[: args.leaves]
     n = w.n_leaves
+    m = w.m
     plan = hps.Plan(w.p, w.boxes(), w.kappa)
     lay = plan.layout
     coef_h, f_h = make_inputs(w, plan)
@@ -319,17 +355,27 @@ def run_gpu(args, rank, ws):
     for name in ("fp32", "fp64"):
         outs[name] = {"S": torch.empty(int(lay.o_sb[-1]), dtype=torch.float64, device="cuda"),
                       "T": torch.empty(int(lay.o_bb[-1]), dtype=torch.float64, device="cuda"),
-                      "h": torch.empty(int(lay.o_nb[-1]), dtype=torch.float64, device="cuda"),
-                      "W": torch.empty(int(lay.o_ni[-1]), dtype=torch.float64, device="cuda"),
+                      "h": torch.empty(int(lay.o_nb[-1]) * m, dtype=torch.float64, device="cuda"),
+                      "W": torch.empty(int(lay.o_ni[-1]) * m, dtype=torch.float64, device="cuda"),
                       "info": torch.empty(n, dtype=torch.int32, device="cuda")}
     tol, kmax = 1e-12, 6
 
-    def step(name):
-        plan.condense(coef, f, m=1, prec=name, tol=tol, kmax=kmax, out=outs[name])
+    graphs = {}
+    if args.graph:
+        from paper_2211_14969_b300 import tune
+        for name in ("fp32", "fp64") if args.prec == "both" else (args.prec,):
+            graphs[name] = tune.CondenseGraph(plan, coef, f, m, prec=name, tol=tol, kmax=kmax, out=outs[name])
 
-    flops = n * leaf_flops(20)
+    def step(name):
+        if name in graphs:
+            graphs[name].replay()
+        else:
+            plan.condense(coef, f, m=m, prec=name, tol=tol, kmax=kmax, out=outs[name])
+
+    flops = float(sum(leaf_flops(int(p), m) for p in w.p))
     pk = peaks()
-    traffic = TRAFFIC_BY_SOURCE.get(source_hash(), {}) if n == 4096 else {}
+    full_p20 = args.workload == "bumps_p20" and not args.leaves
+    traffic = TRAFFIC_BY_SOURCE.get(source_hash(), {}) if full_p20 else {}
     res = {}
     uuid = None
     try:
@@ -341,12 +387,15 @@ def run_gpu(args, rank, ws):
         steps = args.steps
         with ClockSampler(uuid) as cs:
             ms = time_steps(lambda: step(name), steps, args.warmup, ws, stream,
-                            on_start=lambda: plan.set_timing(True))
-        kt = plan.phase_times()        # kernel-only events of the timed calls
-        plan.set_timing(False)
-        info = outs[name]["info"].cpu().numpy()
+                            on_start=None if graphs else (lambda: plan.set_timing(True)))
         per_step = ms / steps
-        kernel_ms = kt[0] / kt[1]
+        if graphs:
+            kernel_ms = per_step          # a replay is the counter reset plus the one kernel
+        else:
+            kt = plan.phase_times()        # kernel-only events of the timed calls
+            plan.set_timing(False)
+            kernel_ms = kt[0] / kt[1]
+        info = outs[name]["info"].cpu().numpy()
         peak = pk["fp64_tflops"] if name == "fp64" else pk["fp32_tflops"]
         achieved = flops / (kernel_ms * 1e-3) / 1e12
         res[name] = {"ms_per_step": per_step, "value": ws * n / (per_step * 1e-3),
@@ -364,7 +413,8 @@ def run_gpu(args, rank, ws):
         plan.close()
         return None
     o64, o32 = outs["fp64"], outs["fp32"]
-    err = {k: rel_leafwise(o32[k], o64[k], n) for k in ("S", "T", "h", "W")}
+    sizes = {"S": lay.sb, "T": lay.bb, "h": lay.nb * m, "W": lay.ni * m}
+    err = {k: rel_leafwise(o32[k], o64[k], sizes[k]) for k in ("S", "T", "h", "W")}
 
     # end to end through the C ABI with host buffers: H2D of the inputs,
     # condensation, D2H of every output, each step
@@ -400,8 +450,9 @@ def run_gpu(args, rank, ws):
         line = {"metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r32["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-                "data": "synthetic (seeded Gaussian bumps, analytic coefficient field), resident in HBM",
-                "config": config_block(w, ws),
+                "data": "synthetic (seeded Gaussian bumps, analytic coefficient fields), resident in HBM",
+                "algorithmic_flops_per_step": flops,
+                "config": config_block(args.workload, w, ws, bool(graphs)),
                 "tflops": r32["tflops"],
                 "precision_path": "fp32 LU/solves + fp64 residual refinement (stop when the estimated error eta_k^2/eta_{k-1} <= 1e-12 in every column, kmax 6)",
                 "roofline": r32["roofline"],
@@ -432,6 +483,9 @@ def main(argv=None):
                     help="profiling: run one path only")
     ap.add_argument("--leaves", type=int, default=0,
                     help="profiling: condense only the first N leaves (no e2e, no CPU leg)")
+    ap.add_argument("--workload", default="bumps_p20", choices=sorted(WORKLOADS),
+                    help="bumps_p20 (default, the headline workload) or another seeded workload")
+    ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the launch")
     args = ap.parse_args(argv)
     rank, ws = dist_setup()
     if args.impl == "reference":

@@ -138,6 +138,19 @@ hps_status hps_merge(hps_plan *plan, int nx, int ny, const double *d_T, const do
 hps_status hps_solve(hps_plan *plan, const double *d_g, const double *d_S, const double *d_W,
                      int m, double *d_u, hps_stream stream);
 
+/* Panel width of the blocked LU for one precision path of this plan:
+ * nb_panel = 0 restores the automatic choice (the widest panel whose shared
+ * memory leaves three CTAs per SM, widened for the mixed path until its
+ * refinement staging fits).  Allowed widths: 4, 8, 16 for HPS_FP64 and 8,
+ * 16, 32 for HPS_MIXED_FP32; a width whose shared memory does not fit an SM
+ * makes the next hps_condense return HPS_ERR_ARG.  Used by autotuners.
+ *
+ * CUDA graphs: hps_condense enqueues one memset and one kernel on the
+ * stream and allocates only when its workspace must grow, so after one
+ * call with the same plan, precision and m it can be captured into a graph
+ * (with timing off) and replayed. */
+hps_status hps_set_blocking(hps_plan *plan, hps_prec prec, int nb_panel);
+
 /* Kernel timing with CUDA events recorded on the launch stream around the
  * condensation kernel of every hps_condense call.  hps_set_timing(plan, 1)
  * enables it and clears the record; hps_phase_times fills up to n values:

@@ -96,6 +96,7 @@ struct hps_plan {
     std::vector<cudaEvent_t> ev;  // pairs around each recorded kernel
     int n_timed = 0;
     int launches = 0;
+    int forced_nb[2] = {0, 0};   // per path (FP64, mixed); 0 = automatic
     // merge tree
     std::vector<Level> levels;
     DevBuf u_leaf;
@@ -290,9 +291,18 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
         return P->fail(HPS_ERR_ARG, "hps_condense: mixed precision needs 4(p-2) + m <= 256");
     const size_t tsize = mixed ? sizeof(float) : sizeof(double);
     const int qmax = P->pmax - 2, nmax = qmax * qmax;
-    const LuBlocking blk = choose_blocking(prec, nmax, P->pmax);
+    LuBlocking blk = choose_blocking(prec, nmax, P->pmax);
+    const int forced = P->forced_nb[mixed ? 1 : 0];
+    if (forced) {
+        blk.nb_panel = forced;
+        if (mixed && (size_t)forced * (blk.ldp + 64) * sizeof(float) <
+                         (size_t)(2 * P->pmax * P->pmax + 4 * nmax) * 8)
+            return P->fail(HPS_ERR_ARG, "hps_condense: forced panel width too narrow for the refinement staging");
+        if (condense_smem(prec, blk) > 227 * 1024)
+            return P->fail(HPS_ERR_ARG, "hps_condense: forced panel width needs more than 227 KB of shared memory");
+    }
     const int per_sm = condense_max_ctas_per_sm(prec, blk);
-    if (per_sm < 1) return P->fail(HPS_ERR_CUDA, "hps_condense: kernel does not fit on an SM");
+    if (per_sm < 1) return P->fail(forced ? HPS_ERR_ARG : HPS_ERR_CUDA, "hps_condense: kernel does not fit on an SM");
     const int grid = std::min(P->n_leaves, P->sms * per_sm);
     long long slot = 0;
     for (int p = P->pmin; p <= P->pmax; ++p) {
@@ -341,6 +351,22 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
         ++P->n_timed;
     }
     P->launches = 1;
+    return HPS_OK;
+}
+
+hps_status hps_set_blocking(hps_plan *P, hps_prec prec, int nb_panel) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (prec == HPS_FP64) {
+        if (nb_panel != 0 && nb_panel != 4 && nb_panel != 8 && nb_panel != 16)
+            return P->fail(HPS_ERR_ARG, "hps_set_blocking: FP64 panel width must be 0, 4, 8 or 16");
+        P->forced_nb[0] = nb_panel;
+    } else if (prec == HPS_MIXED_FP32) {
+        if (nb_panel != 0 && nb_panel != 8 && nb_panel != 16 && nb_panel != 32)
+            return P->fail(HPS_ERR_ARG, "hps_set_blocking: FP32 panel width must be 0, 8, 16 or 32");
+        P->forced_nb[1] = nb_panel;
+    } else {
+        return P->fail(HPS_ERR_ARG, "hps_set_blocking: precision not supported");
+    }
     return HPS_OK;
 }
 

@@ -54,6 +54,7 @@ def load_library():
     L.hps_merge.argtypes = [vp, i, i, vp, vp, i, vp]
     L.hps_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.hps_set_timing.argtypes = [vp, i]
+    L.hps_set_blocking.argtypes = [vp, i, i]
     L.hps_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     L.hps_last_launch_count.argtypes = [vp]
     L.hps_last_error.argtypes = [vp]
@@ -62,7 +63,7 @@ def load_library():
     L.hps_destroy.restype = None
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_merge", "hps_solve",
-                 "hps_set_timing", "hps_phase_times", "hps_last_launch_count"):
+                 "hps_set_timing", "hps_set_blocking", "hps_phase_times", "hps_last_launch_count"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -148,6 +149,11 @@ class Plan:
 
     def solve(self, g, S, W, m, out=None, stream=None):
         return hps_solve(self, g, S, W, m, out, stream)
+
+    def set_blocking(self, prec, nb_panel):
+        """Force the LU panel width of one precision path (0 = automatic)."""
+        prec_id = PREC[prec] if isinstance(prec, str) else int(prec)
+        self.check(load_library().hps_set_blocking(self.handle, prec_id, int(nb_panel)), "hps_set_blocking")
 
     def set_timing(self, on=True):
         self.check(load_library().hps_set_timing(self.handle, int(bool(on))), "hps_set_timing")

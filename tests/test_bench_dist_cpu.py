@@ -80,4 +80,5 @@ def test_algorithmic_flops_per_leaf():
     sys.path.insert(0, ROOT)
     import bench
     assert abs(bench.leaf_flops(20) / 1e6 - 37.98) < 0.01   # LU 22.67 + TRSM 15.12 + DtN 0.19 Mflop
+    assert bench.leaf_flops(20, 1) > bench.leaf_flops(20)
     assert abs(bench.leaf_flops(30) / 1e6 - 459.65) < 0.01

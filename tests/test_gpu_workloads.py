@@ -1,0 +1,87 @@
+"""Full-size workloads on the GPU, each in one launch at its benchmark size,
+with sampled leaves checked against the oracle one by one; plus the
+panel-width autotuner and CUDA-graph replay of the condensation launch."""
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_cases import assert_within, compare_leaves, gpu_inputs
+from paper_2211_14969_b300 import hps, tune
+from paper_2211_14969_b300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-10}
+
+
+def run_full(w, prec, sample=5, seed=0, extra=()):
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    out = plan.condense(coef, f, m=w.m, prec=prec, tol=1e-12, kmax=8)
+    torch.cuda.synchronize()
+    info = out["info"].cpu().numpy()
+    assert (info == 0).all(), np.unique(info, return_counts=True)
+    for k in ("S", "T", "h", "W"):
+        assert torch.isfinite(out[k]).all(), k
+    rng = np.random.default_rng(seed)
+    leaves = sorted(set(rng.integers(0, w.n_leaves, sample).tolist()) | set(extra))
+    recs = compare_leaves(w, plan, out, leaves, TOL[prec])
+    assert_within(recs)
+    return plan, coef, f, out, recs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bumps_p30_full(prec):
+    """32 x 32 leaves, p = 30 (A_ii 784 x 784), kappa = 200."""
+    run_full(WL.bumps_p30(), prec, extra=(0, 1023))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_annulus_p24_full(prec):
+    """The mapped annular sector, 64 x 128 leaves, p = 24, kappa = 400."""
+    run_full(WL.annulus_p24(), prec, extra=(0, 8191))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_uneven_full_m64(prec):
+    """10240 leaves of five orders and 64 body loads in one launch."""
+    w = WL.uneven()
+    extra = [int(np.flatnonzero(w.p == p)[0]) for p in WL.P_SET]
+    run_full(w, prec, sample=4, extra=extra)
+
+
+def test_autotune_picks_a_fitting_width_and_keeps_results(tmp_path):
+    w = WL.uneven(nx=16, ny=8, m=4)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    ref = plan.condense(coef, f, m=w.m, prec="fp32", tol=1e-12, kmax=8)
+    cache = str(tmp_path / "tune.json")
+    nb, times = tune.autotune(plan, coef, f, w.m, prec="fp32", cache_path=cache)
+    assert nb in tune.CANDIDATES["fp32"] and nb in times and len(times) >= 2
+    out = plan.condense(coef, f, m=w.m, prec="fp32", tol=1e-12, kmax=8)
+    torch.cuda.synchronize()
+    for k in ("S", "T", "h", "W"):
+        a, b = out[k], ref[k]
+        assert float((a - b).norm() / b.norm()) < 1e-11, k
+    nb2, _ = tune.autotune(plan, coef, f, w.m, prec="fp32", cache_path=cache)   # from the cache
+    assert nb2 == nb
+    with pytest.raises(hps.HpsError):
+        plan.set_blocking("fp32", 12)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_graph_replay_matches_direct_call(prec):
+    w = WL.uneven(nx=16, ny=16, m=2)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    ref = plan.condense(coef, f, m=w.m, prec=prec, tol=1e-12, kmax=8)
+    torch.cuda.synchronize()
+    ref = {k: v.clone() for k, v in ref.items()}
+    g = tune.CondenseGraph(plan, coef, f, w.m, prec=prec, tol=1e-12, kmax=8)
+    for v in g.out.values():
+        v.zero_()
+    out = g.replay()
+    torch.cuda.synchronize()
+    for k in ("S", "T", "h", "W", "info"):
+        assert torch.equal(out[k], ref[k]), k
