@@ -396,11 +396,13 @@ def run_gpu(args, rank, ws):
             plan.set_timing(False)
             kernel_ms = kt[0] / kt[1]
         info = outs[name]["info"].cpu().numpy()
+        fallback_leaves = plan.fallback_count() if name == "fp32" else 0
         peak = pk["fp64_tflops"] if name == "fp64" else pk["fp32_tflops"]
         achieved = flops / (kernel_ms * 1e-3) / 1e12
         res[name] = {"ms_per_step": per_step, "value": ws * n / (per_step * 1e-3),
                      "tflops": ws * flops / (per_step * 1e-3) / 1e12, "kernel_ms": kernel_ms,
                      "info_nonzero": int((info != 0).sum()),
+                     "fp64_fallback_leaves": int(fallback_leaves),
                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                   "frac": achieved / peak, "traffic": traffic.get(name),
                                   "peak_source": "fp32: 148 SMs x 128 lanes x 2 x max SM clock (unit counts)"
@@ -464,6 +466,7 @@ def run_gpu(args, rank, ws):
                               "clocks": r64["clocks"], "gpu_launches": args.steps},
                 "mixed_vs_fp64_max_leaf_relerr": err,
                 "info_nonzero": {"fp32": r32["info_nonzero"], "fp64": r64["info_nonzero"]},
+                "mixed_leaves_recondensed_in_fp64": r32["fp64_fallback_leaves"],
                 "cpu_baseline": cpu,
                 "parity_vs_oracle_sampled": parity}
         print(json.dumps(line), flush=True)

@@ -108,8 +108,13 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
  *            left after correction k is estimated as eta_k^2 / eta_{k-1}
  *            (linear convergence).  Refinement stops once every column's
  *            estimate is <= tol while still contracting, or after kmax
- *            corrections (then info = -kmax).  kmax = 0 returns the FP32
- *            solution unrefined.  Ignored for HPS_FP64.
+ *            corrections.  kmax = 0 returns the FP32 solution unrefined.
+ *            A leaf that does not converge (typically cond(A_ii) u_fp32
+ *            near 1, e.g. close to an interior Dirichlet resonance) is
+ *            condensed again in FP64 inside the same launch and gets the
+ *            FP64 info code; hps_set_fp64_fallback(plan, 0) turns that off,
+ *            and such a leaf then reports info = -kmax with the last
+ *            iterate.  Ignored for HPS_FP64.
  * Corner rows: with c12 != 0 the interior rows touch the leaf corners, whose
  * columns are dropped (corners are not unknowns). */
 hps_status hps_condense(hps_plan *plan, hps_prec prec, const double *d_coef, const double *d_f,
@@ -150,6 +155,14 @@ hps_status hps_solve(hps_plan *plan, const double *d_g, const double *d_S, const
  * call with the same plan, precision and m it can be captured into a graph
  * (with timing off) and replayed. */
 hps_status hps_set_blocking(hps_plan *plan, hps_prec prec, int nb_panel);
+
+/* Mixed path: re-condense leaves whose refinement did not converge in FP64
+ * (enable = 1, the default) or report them with info = -kmax (enable = 0). */
+hps_status hps_set_fp64_fallback(hps_plan *plan, int enable);
+
+/* Number of leaves the last HPS_MIXED_FP32 hps_condense call re-condensed in
+ * FP64; waits for the stream of that call. */
+hps_status hps_fallback_count(hps_plan *plan, int *count);
 
 /* Kernel timing with CUDA events recorded on the launch stream around the
  * condensation kernel of every hps_condense call.  hps_set_timing(plan, 1)

@@ -515,7 +515,24 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
                 }
                 if (!done) status = -it;
             }
-            write_outputs<double>(P, leaf, L, X, L.r);
+            if (status < 0 && P.fallback) {
+                // Refinement did not converge (a leaf too ill-conditioned for
+                // FP32 factors): condense it again in FP64 in the same slot,
+                // with the double-precision blocking of half the panel width
+                // (its shared memory fits inside this kernel's).
+                const Smem<double> sd = carve<double, NB / 2>(smem_raw, ldp);
+                double *M64 = (double *)slot;
+                __syncthreads();
+                assemble<double>(M64, L, P.dt.dmat + P.dt.doff[L.p], P.kappa2);
+                if (threadIdx.x == 0) sd.misc[1] = 0;
+                __syncthreads();
+                lu_solve<double, NB / 2>(M64, L.LDC, L.n, L.n4, L.C, true, nullptr, ldp, sd);
+                write_outputs<double>(P, leaf, L, M64 + L.n4, L.LDC);
+                status = sd.misc[1];
+                if (threadIdx.x == 0) atomicAdd(P.fallbacks, 1);
+            } else {
+                write_outputs<double>(P, leaf, L, X, L.r);
+            }
             __syncthreads();
             if (threadIdx.x == 0) P.info[leaf] = status;
         }

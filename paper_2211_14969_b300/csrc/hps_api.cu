@@ -97,6 +97,8 @@ struct hps_plan {
     int n_timed = 0;
     int launches = 0;
     int forced_nb[2] = {0, 0};   // per path (FP64, mixed); 0 = automatic
+    int fallback = 1;            // mixed path: re-condense non-converged leaves in FP64
+    cudaStream_t last_stream = nullptr;
     // merge tree
     std::vector<Level> levels;
     DevBuf u_leaf;
@@ -308,7 +310,10 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     for (int p = P->pmin; p <= P->pmax; ++p) {
         const long long q = p - 2, n = q * q, r = 4 * q + m, C = round_up(n, 4) + r, LDC = round_up(C, 4);
         long long b = n * LDC * (long long)tsize;
-        if (mixed) b = round_up(b, 256) + n * r * 8 + 3 * (n + 64) * 4 + round_up(r, 64) * 4 + n * 12 * 4;   // X, perms, eta, node factors
+        if (mixed) {
+            b = round_up(b, 256) + n * r * 8 + 3 * (n + 64) * 4 + round_up(r, 64) * 4 + n * 12 * 4;   // X, perms, eta, node factors
+            b = std::max(b, n * LDC * 8);   // room for the FP64 fallback elimination
+        }
         slot = std::max(slot, round_up(b, 256));
     }
     cudaError_t e = P->work.ensure((size_t)slot * grid);
@@ -335,8 +340,11 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     prm.queue = P->d_queue;
     prm.tol = tol;
     prm.kmax = kmax;
+    prm.fallbacks = P->d_queue + 1;
+    prm.fallback = P->fallback;
     cudaStream_t s = (cudaStream_t)stream;
-    e = cudaMemsetAsync(P->d_queue, 0, sizeof(int), s);
+    e = cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(int), s);
+    P->last_stream = s;
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense: queue reset");
     cudaEvent_t *evp = nullptr;
     if (P->timing && P->n_timed < kMaxTimed) {
@@ -351,6 +359,20 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
         ++P->n_timed;
     }
     P->launches = 1;
+    return HPS_OK;
+}
+
+hps_status hps_set_fp64_fallback(hps_plan *P, int enable) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    P->fallback = enable != 0;
+    return HPS_OK;
+}
+
+hps_status hps_fallback_count(hps_plan *P, int *count) {
+    if (P == nullptr || count == nullptr) return HPS_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(count, P->d_queue + 1, sizeof(int), cudaMemcpyDeviceToHost, P->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->last_stream);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_fallback_count");
     return HPS_OK;
 }
 

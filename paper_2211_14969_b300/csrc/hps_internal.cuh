@@ -52,8 +52,10 @@ struct CondenseParams {
     unsigned char *work;   // per-CTA workspace slots
     long long slot_bytes;
     int *queue;            // work counter, zero at launch
+    int *fallbacks;        // leaves re-condensed in FP64 by the mixed path, zero at launch
     double tol;
     int kmax;
+    int fallback;          // mixed path: redo non-converged leaves in FP64
 };
 
 // Host-side launchers (condense.cu).

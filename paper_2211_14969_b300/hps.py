@@ -55,6 +55,8 @@ def load_library():
     L.hps_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.hps_set_timing.argtypes = [vp, i]
     L.hps_set_blocking.argtypes = [vp, i, i]
+    L.hps_set_fp64_fallback.argtypes = [vp, i]
+    L.hps_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.hps_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     L.hps_last_launch_count.argtypes = [vp]
     L.hps_last_error.argtypes = [vp]
@@ -63,7 +65,8 @@ def load_library():
     L.hps_destroy.restype = None
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_merge", "hps_solve",
-                 "hps_set_timing", "hps_set_blocking", "hps_phase_times", "hps_last_launch_count"):
+                 "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_fallback_count",
+                 "hps_phase_times", "hps_last_launch_count"):
         getattr(L, name).restype = i
     _lib = L
     return L
@@ -154,6 +157,15 @@ class Plan:
         """Force the LU panel width of one precision path (0 = automatic)."""
         prec_id = PREC[prec] if isinstance(prec, str) else int(prec)
         self.check(load_library().hps_set_blocking(self.handle, prec_id, int(nb_panel)), "hps_set_blocking")
+
+    def set_fp64_fallback(self, on=True):
+        """Mixed path: re-condense non-converged leaves in FP64 (default on)."""
+        self.check(load_library().hps_set_fp64_fallback(self.handle, int(bool(on))), "hps_set_fp64_fallback")
+
+    def fallback_count(self):
+        n = ctypes.c_int()
+        self.check(load_library().hps_fallback_count(self.handle, ctypes.byref(n)), "hps_fallback_count")
+        return n.value
 
     def set_timing(self, on=True):
         self.check(load_library().hps_set_timing(self.handle, int(bool(on))), "hps_set_timing")

@@ -39,8 +39,9 @@ class Sub:
         return self.box
 
 
-def run(sub, prec, tol=1e-12, kmax=8, coef_fn=None, load_fn=None, m=None):
+def run(sub, prec, tol=1e-12, kmax=8, coef_fn=None, load_fn=None, m=None, fallback=True):
     plan = hps.Plan(sub.p, sub.box, sub.kappa)
+    plan.set_fp64_fallback(fallback)
     coef, f, _ = gpu_inputs(sub, plan, coef_fn, load_fn)
     out = plan.condense(coef, f, m=sub.m if m is None else m, prec=prec, tol=tol, kmax=kmax)
     torch.cuda.synchronize()
@@ -148,8 +149,12 @@ def test_singular_leaf_reports_info():
 
 def test_refinement_nonconvergence_reported():
     w = WL.bumps(p=12, nx=8, ny=8, kappa=60.0, seed=1, m=1)
-    plan, out = run(Sub(w, [0, 9]), "fp32", tol=0.0, kmax=2)
+    plan, out = run(Sub(w, [0, 9]), "fp32", tol=0.0, kmax=2, fallback=False)
     assert list(out["info"].cpu().numpy()) == [-2, -2]
+    # with the FP64 fallback (default) the same leaves are condensed in FP64
+    plan, out = run(Sub(w, [0, 9]), "fp32", tol=0.0, kmax=2)
+    assert list(out["info"].cpu().numpy()) == [0, 0] and plan.fallback_count() == 2
+    assert_within(compare_leaves(Sub(w, [0, 9]), plan, out, [0, 1], 1e-12))
     plan, out = run(Sub(w, [0, 9]), "fp32", tol=1e-13, kmax=8)
     assert list(out["info"].cpu().numpy()) == [0, 0]
 
