@@ -75,6 +75,14 @@ WORKLOADS = {
 }
 
 
+PEAK_SOURCE = {
+    "fp32": "148 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)",
+    "fp64": "nominal 1.25 TFLOP/s of the part",
+    "bf16": "measured bf16 dense GEMM peak (burst)",
+    "tf32": "measured bf16 peak x nominal tf32/bf16 ratio 1.1/2.25",
+}
+
+
 def make_workload(name):
     from paper_2211_14969_b300 import workloads as WL
     return {"bumps_p20": WL.bumps_p20, "bumps_p30": WL.bumps_p30, "annulus_p24": WL.annulus_p24,
@@ -95,7 +103,12 @@ def peaks():
         sm_mhz = mp.get("sm_max_mhz", sm_mhz)
         hbm = mp.get("hbm_gbs")
     fp32 = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    return {"fp32_tflops": fp32, "fp64_tflops": 1.25, "hbm_gbs": hbm}
+    bf16 = 1738.9
+    if os.path.exists(path):
+        bf16 = mp.get("bf16_tflops", bf16)
+    # TF32 dense: the measured BF16 peak x the nominal TF32 / BF16 ratio (1.1 / 2.25)
+    return {"fp32_tflops": fp32, "fp64_tflops": 1.25, "hbm_gbs": hbm, "bf16_tflops": bf16,
+            "tf32_tflops": bf16 * 1.1 / 2.25}
 
 
 # ---------------------------------------------------------------- distributed
@@ -352,7 +365,8 @@ def run_gpu(args, rank, ws):
     f = torch.from_numpy(f_h).cuda()
     stream = torch.cuda.current_stream()
     outs = {}
-    for name in ("fp32", "fp64"):
+    all_paths = ("fp64", "fp32", "tf32", "bf16")
+    for name in (all_paths if args.prec == "both" else (args.prec,)):
         outs[name] = {"S": torch.empty(int(lay.o_sb[-1]), dtype=torch.float64, device="cuda"),
                       "T": torch.empty(int(lay.o_bb[-1]), dtype=torch.float64, device="cuda"),
                       "h": torch.empty(int(lay.o_nb[-1]) * m, dtype=torch.float64, device="cuda"),
@@ -363,7 +377,7 @@ def run_gpu(args, rank, ws):
     graphs = {}
     if args.graph:
         from paper_2211_14969_b300 import tune
-        for name in ("fp32", "fp64") if args.prec == "both" else (args.prec,):
+        for name in (all_paths if args.prec == "both" else (args.prec,)):
             graphs[name] = tune.CondenseGraph(plan, coef, f, m, prec=name, tol=tol, kmax=kmax, out=outs[name])
 
     def step(name):
@@ -382,7 +396,7 @@ def run_gpu(args, rank, ws):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
     except Exception:
         pass
-    paths = ("fp64", "fp32") if args.prec == "both" else (args.prec,)
+    paths = all_paths if args.prec == "both" else (args.prec,)
     for name in paths:
         steps = args.steps
         with ClockSampler(uuid) as cs:
@@ -396,17 +410,16 @@ def run_gpu(args, rank, ws):
             plan.set_timing(False)
             kernel_ms = kt[0] / kt[1]
         info = outs[name]["info"].cpu().numpy()
-        fallback_leaves = plan.fallback_count() if name == "fp32" else 0
-        peak = pk["fp64_tflops"] if name == "fp64" else pk["fp32_tflops"]
+        fallback_leaves = plan.fallback_count() if name != "fp64" else 0
+        peak = pk[name + "_tflops"]
         achieved = flops / (kernel_ms * 1e-3) / 1e12
         res[name] = {"ms_per_step": per_step, "value": ws * n / (per_step * 1e-3),
                      "tflops": ws * flops / (per_step * 1e-3) / 1e12, "kernel_ms": kernel_ms,
                      "info_nonzero": int((info != 0).sum()),
                      "fp64_fallback_leaves": int(fallback_leaves),
-                     "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": achieved / peak, "traffic": traffic.get(name),
-                                  "peak_source": "fp32: 148 SMs x 128 lanes x 2 x max SM clock (unit counts)"
-                                  if name == "fp32" else "fp64: nominal 1.25 TFLOP/s of the part"},
+                     "roofline": {"bound": "tensor" if name in ("tf32", "bf16") else "alu", "achieved": achieved,
+                                  "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                  "traffic": traffic.get(name), "peak_source": PEAK_SOURCE[name]},
                      "clocks": cs.summary()}
     if args.prec != "both" or args.leaves:
         if rank == 0:
@@ -417,6 +430,15 @@ def run_gpu(args, rank, ws):
     o64, o32 = outs["fp64"], outs["fp32"]
     sizes = {"S": lay.sb, "T": lay.bb, "h": lay.nb * m, "W": lay.ni * m}
     err = {k: rel_leafwise(o32[k], o64[k], sizes[k]) for k in ("S", "T", "h", "W")}
+    tc_paths = {}
+    for name in ("tf32", "bf16"):
+        r = res[name]
+        tc_paths[name + "_path"] = {
+            "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"], "tflops": r["tflops"],
+            "dtype": f"{name} x3 split (hi*hi + hi*lo + lo*hi) on tcgen05, f32 accumulate, + f64 refinement",
+            "roofline": r["roofline"], "clocks": r["clocks"], "gpu_launches": args.steps,
+            "fp64_fallback_leaves": r["fp64_fallback_leaves"], "info_nonzero": r["info_nonzero"],
+            "max_leaf_relerr_vs_fp64": {k: rel_leafwise(outs[name][k], o64[k], sizes[k]) for k in ("S", "T", "h", "W")}}
 
     # end to end through the C ABI with host buffers: H2D of the inputs,
     # condensation, D2H of every output, each step
@@ -465,6 +487,7 @@ def run_gpu(args, rank, ws):
                               "tflops": r64["tflops"], "dtype": "f64", "roofline": r64["roofline"],
                               "clocks": r64["clocks"], "gpu_launches": args.steps},
                 "mixed_vs_fp64_max_leaf_relerr": err,
+                **tc_paths,
                 "info_nonzero": {"fp32": r32["info_nonzero"], "fp64": r64["info_nonzero"]},
                 "mixed_leaves_recondensed_in_fp64": r32["fp64_fallback_leaves"],
                 "cpu_baseline": cpu,
@@ -482,7 +505,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp64"],
+    ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp64", "tf32", "bf16"],
                     help="profiling: run one path only")
     ap.add_argument("--leaves", type=int, default=0,
                     help="profiling: condense only the first N leaves (no e2e, no CPU leg)")

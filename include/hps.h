@@ -57,10 +57,14 @@ typedef enum {
 
 typedef enum {
     HPS_FP64 = 0,        /* everything in FP64 */
-    HPS_MIXED_FP32 = 1,  /* FP32 LU/TRSM, FP64 residual + iterative refinement */
-    HPS_MIXED_TF32 = 2,  /* reserved: TF32 tensor-core LU + FP64 refinement */
-    HPS_MIXED_BF16 = 3   /* reserved: BF16 tensor-core LU + FP64 refinement */
+    HPS_MIXED_FP32 = 1,  /* FP32 LU/TRSM, FP64-accurate residual + iterative refinement */
+    HPS_MIXED_TF32 = 2,  /* as HPS_MIXED_FP32, the LU's trailing updates on the tensor
+                            cores (tcgen05, TF32 inputs split hi + lo, FP32 accumulation) */
+    HPS_MIXED_BF16 = 3   /* as HPS_MIXED_TF32 with BF16 inputs split hi + lo */
 } hps_prec;
+
+/* info code of a leaf whose tensor-core wait timed out (HPS_MIXED_TF32/BF16) */
+#define HPS_INFO_TC_TIMEOUT (-1073741824)
 
 #define HPS_PMIN 4
 #define HPS_PMAX 42

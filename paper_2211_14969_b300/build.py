@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhps.so")
 SOURCES = ["hps_api.cu", "condense.cu", "merge.cu", "noalloc.cu"]
-HEADERS = ["hps_internal.cuh", "dense_lu.cuh", "merge.cuh"]
+HEADERS = ["hps_internal.cuh", "dense_lu.cuh", "merge.cuh", "tc_gemm.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -456,13 +456,33 @@ __device__ bool refine_update(T *__restrict__ M, double *__restrict__ X, float *
     return __syncthreads_or(bad) == 0;
 }
 
-template <typename T, int NB, bool MIXED>
+// Offset of the tensor-core operand buffers behind the LU's shared memory.
+__host__ __device__ inline size_t tc_smem_offset(size_t lu_bytes) { return (lu_bytes + 1023) & ~(size_t)1023; }
+
+template <typename T, int NB, bool MIXED, int TCK = 0>
 __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const Smem<T> sm = carve<T, NB>(smem_raw, P.blk.ldp);
     const int ldp = P.blk.ldp;
     unsigned char *slot = P.work + (long long)blockIdx.x * P.slot_bytes;
     T *M = (T *)slot;
+    tc::TcState tcs{};
+    const tc::TcState *tsp = nullptr;
+    if constexpr (TCK != 0) {
+        unsigned char *b = smem_raw + tc_smem_offset(smem_bytes_for<T, NB>(ldp));
+        constexpr int EB = tc::In<TCK>::BYTES;
+        tcs.a_hi = b;
+        tcs.a_lo = b + tc::TM * NB * EB;
+        tcs.b_hi = b + 2 * tc::TM * NB * EB;
+        tcs.b_lo = tcs.b_hi + tc::TN * NB * EB;
+        unsigned char *tail = b + tc::operand_bytes<TCK>(NB);
+        tcs.mbar = (uint64_t *)tail;
+        tcs.tmem = (uint32_t *)(tail + 8);
+        tcs.phase = (uint32_t *)(tail + 12);
+        tcs.err = (int *)(tail + 16);
+        tc::tmem_alloc(tcs);
+        tsp = &tcs;
+    }
     for (;;) {
         if (threadIdx.x == 0) {
             const int t = atomicAdd(P.queue, 1);
@@ -472,6 +492,9 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
         __syncthreads();
         const int leaf = sm.misc[0];
         if (leaf < 0) break;
+        if constexpr (TCK != 0) {
+            if (threadIdx.x == 0) *tcs.err = 0;
+        }
         LeafInfo L = leaf_info(P, leaf);
         L.flags = leaf_flags(L);
         const T *Dw = (const T *)(sizeof(T) == 4 ? (const void *)P.dt.dmat32 : (const void *)P.dt.dmat) + P.dt.doff[L.p];
@@ -486,7 +509,7 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
             const long long mbytes = (((long long)L.n * L.LDC * (long long)sizeof(T)) + 255) & ~255LL;
             double *X = (double *)(slot + mbytes);
             int *perm_g = (int *)(X + (long long)L.n * L.r);   // 3 NB ints per panel
-            lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm);
+            lu_solve<T, NB, TCK>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm, tsp);
             float *eta = (float *)(perm_g + 3 * (L.n + 64));
             float *nf = eta + ((L.r + 63) & ~63);                 // 12 floats per interior node
             const float *Dhi = P.dt.dmat32 + P.dt.doff[L.p], *Dlo = P.dt.dmat_lo + P.dt.doff[L.p];
@@ -503,6 +526,9 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
             for (int c = threadIdx.x; c < L.r; c += NT) eta[c] = 1.0f;
             __syncthreads();
             int status = sm.misc[1];
+            if constexpr (TCK != 0) {
+                if (*tcs.err) status = HPS_INFO_TC_TIMEOUT;   // a tensor-core wait timed out
+            }
             if (status == 0 && P.kmax > 0) {
                 int it = 0;
                 bool done = false;
@@ -515,7 +541,7 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
                 }
                 if (!done) status = -it;
             }
-            if (status < 0 && P.fallback) {
+            if (status < 0 && status != HPS_INFO_TC_TIMEOUT && P.fallback) {
                 // Refinement did not converge (a leaf too ill-conditioned for
                 // FP32 factors): condense it again in FP64 in the same slot,
                 // with the double-precision blocking of half the panel width
@@ -538,6 +564,7 @@ __global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
         }
         __syncthreads();
     }
+    if constexpr (TCK != 0) tc::tmem_free(tcs);
 }
 
 template <int NB>
@@ -586,13 +613,19 @@ int occupancy(K kernel, size_t smem) {
     return nb;
 }
 
-template <typename T, int NB, bool MIXED>
+template <typename T, int NB, int TCK>
+size_t kernel_smem(int ldp) {
+    if constexpr (TCK == 0) return smem_of<T, NB>(ldp);
+    else return tc_smem_offset(smem_of<T, NB>(ldp)) + tc::operand_bytes<TCK>(NB) + 64;
+}
+
+template <typename T, int NB, bool MIXED, int TCK = 0>
 cudaError_t launch_one(const CondenseParams &prm, int grid, cudaStream_t s) {
-    const size_t smem = smem_of<T, NB>(prm.blk.ldp);
-    cudaError_t e = cudaFuncSetAttribute(condense_kernel<T, NB, MIXED>,
+    const size_t smem = kernel_smem<T, NB, TCK>(prm.blk.ldp);
+    cudaError_t e = cudaFuncSetAttribute(condense_kernel<T, NB, MIXED, TCK>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    condense_kernel<T, NB, MIXED><<<grid, NT, smem, s>>>(prm);
+    condense_kernel<T, NB, MIXED, TCK><<<grid, NT, smem, s>>>(prm);
     return cudaGetLastError();
 }
 
@@ -623,42 +656,61 @@ LuBlocking choose_blocking(int prec, int nmax, int pmax) {
 }
 
 size_t condense_smem(int prec, const LuBlocking &b) {
-    if (prec == HPS_FP64)
-        return b.nb_panel == 16 ? smem_of<double, 16>(b.ldp) : b.nb_panel == 8 ? smem_of<double, 8>(b.ldp) : smem_of<double, 4>(b.ldp);
-    return b.nb_panel == 32 ? smem_of<float, 32>(b.ldp) : b.nb_panel == 16 ? smem_of<float, 16>(b.ldp) : smem_of<float, 8>(b.ldp);
+    const int nb = b.nb_panel;
+    switch (prec) {
+        case HPS_FP64:
+            return nb == 16 ? smem_of<double, 16>(b.ldp) : nb == 8 ? smem_of<double, 8>(b.ldp) : smem_of<double, 4>(b.ldp);
+        case HPS_MIXED_TF32:
+            return nb == 32 ? kernel_smem<float, 32, tc::KIND_TF32>(b.ldp)
+                 : nb == 16 ? kernel_smem<float, 16, tc::KIND_TF32>(b.ldp) : kernel_smem<float, 8, tc::KIND_TF32>(b.ldp);
+        case HPS_MIXED_BF16:
+            return nb == 32 ? kernel_smem<float, 32, tc::KIND_BF16>(b.ldp)
+                 : nb == 16 ? kernel_smem<float, 16, tc::KIND_BF16>(b.ldp) : kernel_smem<float, 8, tc::KIND_BF16>(b.ldp);
+        default:
+            return nb == 32 ? smem_of<float, 32>(b.ldp) : nb == 16 ? smem_of<float, 16>(b.ldp) : smem_of<float, 8>(b.ldp);
+    }
 }
 
 int condense_max_ctas_per_sm(int prec, const LuBlocking &b) {
     const size_t smem = condense_smem(prec, b);
-    if (prec == HPS_FP64) {
-        switch (b.nb_panel) {
-            case 16: return occupancy(condense_kernel<double, 16, false>, smem);
-            case 8: return occupancy(condense_kernel<double, 8, false>, smem);
-            default: return occupancy(condense_kernel<double, 4, false>, smem);
-        }
-    }
-    switch (b.nb_panel) {
-        case 32: return occupancy(condense_kernel<float, 32, true>, smem);
-        case 16: return occupancy(condense_kernel<float, 16, true>, smem);
-        default: return occupancy(condense_kernel<float, 8, true>, smem);
+    const int nb = b.nb_panel;
+    switch (prec) {
+        case HPS_FP64:
+            return nb == 16 ? occupancy(condense_kernel<double, 16, false>, smem)
+                 : nb == 8 ? occupancy(condense_kernel<double, 8, false>, smem) : occupancy(condense_kernel<double, 4, false>, smem);
+        case HPS_MIXED_TF32:
+            return nb == 32 ? occupancy(condense_kernel<float, 32, true, tc::KIND_TF32>, smem)
+                 : nb == 16 ? occupancy(condense_kernel<float, 16, true, tc::KIND_TF32>, smem)
+                            : occupancy(condense_kernel<float, 8, true, tc::KIND_TF32>, smem);
+        case HPS_MIXED_BF16:
+            return nb == 32 ? occupancy(condense_kernel<float, 32, true, tc::KIND_BF16>, smem)
+                 : nb == 16 ? occupancy(condense_kernel<float, 16, true, tc::KIND_BF16>, smem)
+                            : occupancy(condense_kernel<float, 8, true, tc::KIND_BF16>, smem);
+        default:
+            return nb == 32 ? occupancy(condense_kernel<float, 32, true>, smem)
+                 : nb == 16 ? occupancy(condense_kernel<float, 16, true>, smem) : occupancy(condense_kernel<float, 8, true>, smem);
     }
 }
 
 cudaError_t launch_condense(int prec, const CondenseParams &prm, int grid, cudaStream_t s) {
-    if (prec == HPS_FP64) {
-        switch (prm.blk.nb_panel) {
-            case 16: return launch_one<double, 16, false>(prm, grid, s);
-            case 8: return launch_one<double, 8, false>(prm, grid, s);
-            default: return launch_one<double, 4, false>(prm, grid, s);
-        }
-    }
-    switch (prm.blk.nb_panel) {
-        case 32: return launch_one<float, 32, true>(prm, grid, s);
-        case 16: return launch_one<float, 16, true>(prm, grid, s);
-        default: return launch_one<float, 8, true>(prm, grid, s);
+    const int nb = prm.blk.nb_panel;
+    switch (prec) {
+        case HPS_FP64:
+            return nb == 16 ? launch_one<double, 16, false>(prm, grid, s)
+                 : nb == 8 ? launch_one<double, 8, false>(prm, grid, s) : launch_one<double, 4, false>(prm, grid, s);
+        case HPS_MIXED_TF32:
+            return nb == 32 ? launch_one<float, 32, true, tc::KIND_TF32>(prm, grid, s)
+                 : nb == 16 ? launch_one<float, 16, true, tc::KIND_TF32>(prm, grid, s)
+                            : launch_one<float, 8, true, tc::KIND_TF32>(prm, grid, s);
+        case HPS_MIXED_BF16:
+            return nb == 32 ? launch_one<float, 32, true, tc::KIND_BF16>(prm, grid, s)
+                 : nb == 16 ? launch_one<float, 16, true, tc::KIND_BF16>(prm, grid, s)
+                            : launch_one<float, 8, true, tc::KIND_BF16>(prm, grid, s);
+        default:
+            return nb == 32 ? launch_one<float, 32, true>(prm, grid, s)
+                 : nb == 16 ? launch_one<float, 16, true>(prm, grid, s) : launch_one<float, 8, true>(prm, grid, s);
     }
 }
-
 
 cudaError_t launch_dense_solve(double *base, long long stride, int n, int n4, int C, int LDC, int batch,
                                int *info, cudaStream_t s) {

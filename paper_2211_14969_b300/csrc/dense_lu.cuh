@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include "hps_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace hps {
 namespace lu {
@@ -448,11 +449,103 @@ __device__ __forceinline__ void gemm_sub(T *__restrict__ Mg, int LDC, int r0, in
     }
 }
 
+// C[r0:r1, c0:c0+cw] -= A * B on the tensor cores (see tc_gemm.cuh): A from
+// the shared panel (column-major, ld lda, rows offset arow0), B = the shared
+// chunk (K x CH, row-major), K <= NB (zero-padded to NB).
+template <int KIND, int NB>
+__device__ void gemm_sub_tc(float *__restrict__ Mg, int LDC, int r0, int r1, int c0, int cw,
+                            const float *__restrict__ A, int lda, int arow0, const float *__restrict__ B, int K,
+                            const tc::TcState &ts) {
+    using namespace tc;
+    constexpr int EB = In<KIND>::BYTES, PER = 16 / EB, KS = In<KIND>::KSTEP;
+    constexpr int CH = Cfg<float, NB>::CH;
+    static_assert(CH == TN, "chunk width must equal the MMA tile width");
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // B (the chunk's U12 rows, as TN x NB K-major): element (c, k) = B[k][c]
+    for (int e = tid; e < TN * (NB / PER); e += NT) {   // one core-matrix row (PER k) per thread
+        const int c = e % TN, g = e / TN;
+        float x[PER];
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int k = g * PER + t;
+            x[t] = (k < K && c < cw) ? B[k * CH + c] : 0.0f;
+        }
+        const int off = kmajor_off<KIND>(c, g * PER, NB);
+        SplitRow<KIND>::store(ts.b_hi + off, ts.b_lo + off, x);
+    }
+    const uint32_t idesc = instr_desc<KIND>();
+    const uint32_t lbo = 128, sbo = (NB / PER) * 128;
+    for (int rb = r0; rb < r1; rb += TM) {
+        for (int e = tid; e < TM * (NB / PER); e += NT) {
+            const int r = e % TM, g = e / TM, row = rb + r;
+            float x[PER];
+#pragma unroll
+            for (int t = 0; t < PER; ++t) {
+                const int k = g * PER + t;
+                x[t] = (row < r1 && k < K) ? A[k * lda + (row - arow0)] : 0.0f;
+            }
+            const int off = kmajor_off<KIND>(r, g * PER, NB);
+            SplitRow<KIND>::store(ts.a_hi + off, ts.a_lo + off, x);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t tmem = *ts.tmem, phase = *ts.phase;
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < NB / KS; ++ks) {
+                const uint32_t step = ks * (KS / PER) * 128;
+                const uint64_t ah = smem_desc(smem_addr(ts.a_hi) + step, lbo, sbo);
+                const uint64_t al = smem_desc(smem_addr(ts.a_lo) + step, lbo, sbo);
+                const uint64_t bh = smem_desc(smem_addr(ts.b_hi) + step, lbo, sbo);
+                const uint64_t bl = smem_desc(smem_addr(ts.b_lo) + step, lbo, sbo);
+                mma(tmem, ah, bh, idesc, ks > 0, KIND);
+                mma(tmem, ah, bl, idesc, 1, KIND);
+                mma(tmem, al, bh, idesc, 1, KIND);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_addr(ts.mbar)));
+        }
+        const bool ok = __all_sync(0xffffffffu, wait_mma(ts, phase));
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (ok) {
+            const int row = rb + warp * 32 + lane;
+            float *crow = Mg + (long long)min(row, r1 - 1) * LDC + c0;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float v[32];
+                ld_row32(tmem + ((uint32_t)(warp * 32) << 16) + half * 32, v);
+                if (row < r1) {
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const int c = half * 32 + g * 4;
+                        if (c < cw) {
+                            float4 cv = *(float4 *)(crow + c);
+                            cv.x -= v[g * 4];
+                            cv.y -= v[g * 4 + 1];
+                            cv.z -= v[g * 4 + 2];
+                            cv.w -= v[g * 4 + 3];
+                            *(float4 *)(crow + c) = cv;
+                        }
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicExch(ts.err, 1);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (tid == 0) *ts.phase = phase ^ 1u;
+    }
+}
+
 // Apply the panel at rows k0.. (permutation, unit-lower solve, trailing
 // update) to columns [cstart, C) of M.
-template <typename T, int NB>
+template <typename T, int NB, int TCK = 0>
 __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, int nbk, int cstart, int ldp,
-                            const Smem<T> &sm) {
+                            const Smem<T> &sm, const tc::TcState *ts = nullptr) {
     using CF = Cfg<T, NB>;
     using V = typename Vec<T>::type;
     constexpr int CH = CF::CH, HV = CF::HV;
@@ -515,7 +608,12 @@ __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, in
             }
         }
         __syncthreads();
-        gemm_sub<T, NB>(M, LDC, k0 + nbk, n, c0, cw, sm.Ps, ldp, k0, sm.Us, nbk);
+        if constexpr (TCK != 0) {
+            if (ts) gemm_sub_tc<TCK, NB>(M, LDC, k0 + nbk, n, c0, cw, sm.Ps, ldp, k0, sm.Us, nbk, *ts);
+            else gemm_sub<T, NB>(M, LDC, k0 + nbk, n, c0, cw, sm.Ps, ldp, k0, sm.Us, nbk);
+        } else {
+            gemm_sub<T, NB>(M, LDC, k0 + nbk, n, c0, cw, sm.Ps, ldp, k0, sm.Us, nbk);
+        }
         __syncthreads();
     }
 }
@@ -525,9 +623,9 @@ __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, in
 // perm_g is given, factoring stores each panel's permutation there (3 NB
 // ints per panel: top-row sources, displaced sources, displaced targets)
 // and replaying (factor = false) reads it back.
-template <typename T, int NB>
+template <typename T, int NB, int TCK = 0>
 __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool factor, int *perm_g, int ldp,
-                         const Smem<T> &sm) {
+                         const Smem<T> &sm, const tc::TcState *ts = nullptr) {
     using CF = Cfg<T, NB>;
     using V = typename Vec<T>::type;
     constexpr int CH = CF::CH, HV = CF::HV;
@@ -557,7 +655,9 @@ __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool 
                 }
         }
         const int cstart = factor ? (k0 + nbk < n ? k0 + nbk : n4) : n4;
-        apply_panel<T, NB>(M, LDC, n, C, k0, nbk, cstart, ldp, sm);
+        // the factorization's trailing updates go to the tensor cores when
+        // enabled; the right-hand-only replays stay on the FP32 pipe
+        apply_panel<T, NB, TCK>(M, LDC, n, C, k0, nbk, cstart, ldp, sm, factor ? ts : nullptr);
     }
 
     // U X = Y for the right-hand columns, block rows from the bottom

@@ -279,8 +279,8 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
                         double tol, int kmax, double *d_S, double *d_T, double *d_h, double *d_W,
                         int *d_info, hps_stream stream) {
     if (P == nullptr) return HPS_ERR_ARG;
-    if (prec != HPS_FP64 && prec != HPS_MIXED_FP32)
-        return P->fail(HPS_ERR_ARG, "hps_condense: precision not supported (use HPS_FP64 or HPS_MIXED_FP32)");
+    if (prec != HPS_FP64 && prec != HPS_MIXED_FP32 && prec != HPS_MIXED_TF32 && prec != HPS_MIXED_BF16)
+        return P->fail(HPS_ERR_ARG, "hps_condense: unknown precision");
     if (d_coef == nullptr || d_T == nullptr || d_info == nullptr)
         return P->fail(HPS_ERR_ARG, "hps_condense: d_coef, d_T and d_info are required");
     if (m < 0) return P->fail(HPS_ERR_ARG, "hps_condense: m < 0");
@@ -382,7 +382,7 @@ hps_status hps_set_blocking(hps_plan *P, hps_prec prec, int nb_panel) {
         if (nb_panel != 0 && nb_panel != 4 && nb_panel != 8 && nb_panel != 16)
             return P->fail(HPS_ERR_ARG, "hps_set_blocking: FP64 panel width must be 0, 4, 8 or 16");
         P->forced_nb[0] = nb_panel;
-    } else if (prec == HPS_MIXED_FP32) {
+    } else if (prec == HPS_MIXED_FP32 || prec == HPS_MIXED_TF32 || prec == HPS_MIXED_BF16) {
         if (nb_panel != 0 && nb_panel != 8 && nb_panel != 16 && nb_panel != 32)
             return P->fail(HPS_ERR_ARG, "hps_set_blocking: FP32 panel width must be 0, 8, 16 or 32");
         P->forced_nb[1] = nb_panel;
