@@ -137,24 +137,42 @@ template <typename T> struct PanelCfg;
 template <> struct PanelCfg<float> { static constexpr int W = 8, RMAX = 8; };
 template <> struct PanelCfg<double> { static constexpr int W = 8, RMAX = 4; };
 
+// Magnitude key for the pivot search: |x| itself for float; for double the
+// bit pattern with the sign cleared (non-negative IEEE doubles order like
+// their bit patterns), so the comparisons stay off the FP64 pipe.  NaN keys
+// order above every finite value.
+template <typename T> struct MagKey;
+template <> struct MagKey<float> {
+    using K = float;
+    __device__ static K of(float x) { return fabsf(x); }
+    __device__ static K none() { return -1.0f; }
+};
+template <> struct MagKey<double> {
+    using K = long long;
+    __device__ static K of(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+    __device__ static K none() { return -1LL; }
+};
+
 // Argmax of |value| over the CTA: (best, row) partials per thread -> the
 // row index every thread agrees on (largest magnitude, first row on ties).
 template <typename T>
-__device__ __forceinline__ int block_argmax(T best, int bi, const Smem<T> &sm) {
+__device__ __forceinline__ int block_argmax(typename MagKey<T>::K best, int bi, const Smem<T> &sm) {
+    using K = typename MagKey<T>::K;
+    K *redk = (K *)sm.redv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const K ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    if (lane == 0) { sm.redv[warp] = best; sm.redi[warp] = bi; }
+    if (lane == 0) { redk[warp] = best; sm.redi[warp] = bi; }
     __syncthreads();
-    best = sm.redv[0];
+    best = redk[0];
     bi = sm.redi[0];
 #pragma unroll
     for (int w = 1; w < NWARP; ++w) {
-        const T ov = sm.redv[w];
+        const K ov = redk[w];
         const int oi = sm.redi[w];
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
@@ -191,10 +209,10 @@ __device__ void panel_factor(T *__restrict__ P, int ldp, int mp, int nbk, int k0
     const int tid = threadIdx.x;
     if (mp > RMAX * NT) {
         for (int j = 0; j < nbk; ++j) {
-            T best = T(-1);
+            typename MagKey<T>::K best = MagKey<T>::none();
             int bi = 0x7fffffff;
             for (int i = j + tid; i < mp; i += NT) {
-                const T v = absval(P[j * ldp + i]);
+                const auto v = MagKey<T>::of(P[j * ldp + i]);
                 if (v > best) { best = v; bi = i; }
             }
             bi = block_argmax<T>(best, bi, sm);
@@ -241,12 +259,12 @@ __device__ void panel_factor(T *__restrict__ P, int ldp, int mp, int nbk, int k0
         for (int jj = 0; jj < W; ++jj) {
             if (jj < w) {
                 const int j = s0 + jj;
-                T best = T(-1);
+                typename MagKey<T>::K best = MagKey<T>::none();
                 int bi = 0x7fffffff;
 #pragma unroll
                 for (int t = 0; t < RMAX; ++t) {
                     const int i = s0 + tid + t * NT;
-                    const T v = absval(a[t][jj]);
+                    const auto v = MagKey<T>::of(a[t][jj]);
                     if (i >= j && i < mp && v > best) { best = v; bi = i; }
                 }
                 bi = block_argmax<T>(best, bi, sm);
@@ -390,11 +408,35 @@ __device__ __forceinline__ void gemm_sub(T *__restrict__ Mg, int LDC, int r0, in
         const bool va = sa < r1, vb = sb < r1;
         if (!va && !vb) continue;
         const int ia = (va ? sa : r0) - arow0, ib = (vb ? sb : r0) - arow0;
+        // FP64: accumulate straight into the loaded C tile (C -= a b per
+        // step), so the FP64 pipe carries no separate subtraction; FP32:
+        // accumulate the product from zero and subtract once (C - sum ab
+        // keeps the FP32 factors measurably more accurate).
+        constexpr bool INPLACE = sizeof(T) == 8;
         T acc[2 * HV][2 * HV];
 #pragma unroll
         for (int u = 0; u < 2 * HV; ++u)
 #pragma unroll
             for (int v = 0; v < 2 * HV; ++v) acc[u][v] = T(0);
+        if constexpr (INPLACE) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int s = half ? sb : sa;
+#pragma unroll
+                for (int u = 0; u < HV; ++u) {
+                    const T *row = Mg + (long long)min(s + u, r1 - 1) * LDC + c0;
+#pragma unroll
+                    for (int hc = 0; hc < 2; ++hc) {
+                        const int c = hc ? cB : cA;
+                        const V cv = *(const V *)(row + (c < cw ? c : 0));
+                        const T *pc = (const T *)&cv;
+#pragma unroll
+                        for (int v = 0; v < HV; ++v) acc[half * HV + u][hc * HV + v] = pc[v];
+                    }
+                }
+            }
+        }
+        const T sgn = INPLACE ? T(-1) : T(1);
 #pragma unroll 4
         for (int kk = 0; kk < K; ++kk) {
             const V a0 = *(const V *)(A + kk * lda + ia);
@@ -405,14 +447,38 @@ __device__ __forceinline__ void gemm_sub(T *__restrict__ Mg, int LDC, int r0, in
             const T *pb0 = (const T *)&b0, *pb1 = (const T *)&b1;
 #pragma unroll
             for (int u = 0; u < HV; ++u) {
+                const T x0 = sgn * pa0[u], x1 = sgn * pa1[u];
 #pragma unroll
                 for (int v = 0; v < HV; ++v) {
-                    acc[u][v] = fma(pa0[u], pb0[v], acc[u][v]);
-                    acc[u][HV + v] = fma(pa0[u], pb1[v], acc[u][HV + v]);
-                    acc[HV + u][v] = fma(pa1[u], pb0[v], acc[HV + u][v]);
-                    acc[HV + u][HV + v] = fma(pa1[u], pb1[v], acc[HV + u][HV + v]);
+                    acc[u][v] = fma(x0, pb0[v], acc[u][v]);
+                    acc[u][HV + v] = fma(x0, pb1[v], acc[u][HV + v]);
+                    acc[HV + u][v] = fma(x1, pb0[v], acc[HV + u][v]);
+                    acc[HV + u][HV + v] = fma(x1, pb1[v], acc[HV + u][HV + v]);
                 }
             }
+        }
+        if constexpr (INPLACE) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int s = half ? sb : sa;
+#pragma unroll
+                for (int u = 0; u < HV; ++u) {
+                    const int r = s + u;
+                    if (r >= r1) continue;
+                    T *row = Mg + (long long)r * LDC + c0;
+#pragma unroll
+                    for (int hc = 0; hc < 2; ++hc) {
+                        const int c = hc ? cB : cA;
+                        if (c >= cw) continue;
+                        V cv;
+                        T *pc = (T *)&cv;
+#pragma unroll
+                        for (int v = 0; v < HV; ++v) pc[v] = acc[half * HV + u][hc * HV + v];
+                        *(V *)(row + c) = cv;
+                    }
+                }
+            }
+            continue;
         }
         // C -= acc, one half of the rows at a time: the half's 2HV vector
         // loads are all issued before the first subtraction
