@@ -462,6 +462,35 @@ def run_gpu(args, rank, ws):
         e2e = {"value": ws * n / (ms_e2e / steps_e2e * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # the uneven workload: the fused launch against one launch per order
+    # (a separate plan for each p, run back to back on the same stream)
+    per_order = None
+    if args.workload == "uneven" and not args.leaves and rank == 0:
+        per_order = {}
+        subs = []
+        for p in sorted(set(int(v) for v in w.p)):
+            idx = np.flatnonzero(np.asarray(w.p) == p)
+            sp = hps.Plan(w.p[idx], w.boxes()[idx], w.kappa)
+            sl = sp.layout
+            gx = np.concatenate([np.arange(6 * int(lay.o_p2[l]), 6 * int(lay.o_p2[l + 1])) for l in idx])
+            gf = np.concatenate([np.arange(int(lay.o_p2[l]) * m, int(lay.o_p2[l + 1]) * m) for l in idx])
+            c_sub, f_sub = coef[torch.from_numpy(gx).cuda()], f[torch.from_numpy(gf).cuda()]
+            o = {"S": torch.empty(int(sl.o_sb[-1]), dtype=torch.float64, device="cuda"),
+                 "T": torch.empty(int(sl.o_bb[-1]), dtype=torch.float64, device="cuda"),
+                 "h": torch.empty(int(sl.o_nb[-1]) * m, dtype=torch.float64, device="cuda"),
+                 "W": torch.empty(int(sl.o_ni[-1]) * m, dtype=torch.float64, device="cuda"),
+                 "info": torch.empty(len(idx), dtype=torch.int32, device="cuda")}
+            subs.append((sp, c_sub, f_sub, o))
+        for name in ("fp64", "fp32"):
+            def per_order_step():
+                for sp, c_sub, f_sub, o in subs:
+                    sp.condense(c_sub, f_sub, m=m, prec=name, tol=tol, kmax=kmax, out=o)
+            ms_po = time_steps(per_order_step, max(2, args.steps // 2), 1, 1, stream) / max(2, args.steps // 2)
+            per_order[name] = {"ms_per_step": ms_po, "value": n / (ms_po * 1e-3), "launches": len(subs),
+                               "fused_ms_per_step": res[name]["ms_per_step"]}
+        for sp, *_ in subs:
+            sp.close()
+
     line = None
     if rank == 0:
         cpu = None
@@ -492,6 +521,8 @@ def run_gpu(args, rank, ws):
                 "mixed_leaves_recondensed_in_fp64": r32["fp64_fallback_leaves"],
                 "cpu_baseline": cpu,
                 "parity_vs_oracle_sampled": parity}
+        if per_order is not None:
+            line["per_order_launches"] = per_order
         print(json.dumps(line), flush=True)
     plan.close()
     return line

@@ -137,3 +137,17 @@ def test_merge_argument_errors():
         g = torch.zeros(16, dtype=torch.float64, device="cuda")
         S = torch.zeros(int(plan.layout.o_sb[-1]), dtype=torch.float64, device="cuda")
         plan.solve(g, S, None, 1)             # solve before merge
+
+
+@pytest.mark.parametrize("nx,ny,p", [(32, 32, 8), (16, 32, 10)])
+def test_larger_and_rectangular_grids_match_oracle(nx, ny, p):
+    """10 and 9 merge levels (top interfaces of 192 and 256 nodes), square
+    and 1:2 grids, variable b and bumps, against the oracle's merge tree."""
+    w = WL.bumps(p=p, nx=nx, ny=ny, kappa=30.0, seed=6, m=1)
+    w.dirichlet = "planewave"
+    u_gpu = gpu_pipeline(w)
+    sol, _, _ = oracle_pipeline(w)
+    u_ora = grid_from_sol(sol, p)
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    assert rel(u_gpu[:, mask], u_ora[:, mask]) < 1e-11
