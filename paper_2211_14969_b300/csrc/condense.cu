@@ -460,7 +460,7 @@ __device__ bool refine_update(T *__restrict__ M, double *__restrict__ X, float *
 __host__ __device__ inline size_t tc_smem_offset(size_t lu_bytes) { return (lu_bytes + 1023) & ~(size_t)1023; }
 
 template <typename T, int NB, bool MIXED, int TCK = 0>
-__global__ void __launch_bounds__(NT, 4) condense_kernel(CondenseParams P) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(CondenseParams P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const Smem<T> sm = carve<T, NB>(smem_raw, P.blk.ldp);
     const int ldp = P.blk.ldp;

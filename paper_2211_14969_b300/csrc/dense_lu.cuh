@@ -39,7 +39,10 @@ template <typename T, int NB_>
 struct Cfg {
     static constexpr int NB = NB_;
     static constexpr int HV = Vec<T>::N;   // elements per 16-byte vector
-    static constexpr int TY = 16, TX = 8;  // thread grid of the update tile
+    // thread grid of the update tile: FP32 8 x 16 (64-row passes over
+    // 128-column chunks, so a right-hand block of up to 128 columns is one
+    // chunk), FP64 16 x 8 (64 x 32)
+    static constexpr int TY = sizeof(T) == 4 ? 8 : 16, TX = NT / TY;
     static constexpr int BM = 2 * TY * HV;  // rows per update pass
     static constexpr int CH = 2 * TX * HV;  // columns per chunk
 };
@@ -525,8 +528,10 @@ __device__ void gemm_sub_tc(float *__restrict__ Mg, int LDC, int r0, int r1, int
     using namespace tc;
     constexpr int EB = In<KIND>::BYTES, PER = 16 / EB, KS = In<KIND>::KSTEP;
     constexpr int CH = Cfg<float, NB>::CH;
-    static_assert(CH == TN, "chunk width must equal the MMA tile width");
+    static_assert(CH % TN == 0, "chunk width must be a multiple of the MMA tile width");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int cb = 0; cb < cw; cb += TN) {
+    const int cwh = min(TN, cw - cb);
     // B (the chunk's U12 rows, as TN x NB K-major): element (c, k) = B[k][c]
     for (int e = tid; e < TN * (NB / PER); e += NT) {   // one core-matrix row (PER k) per thread
         const int c = e % TN, g = e / TN;
@@ -534,7 +539,7 @@ __device__ void gemm_sub_tc(float *__restrict__ Mg, int LDC, int r0, int r1, int
 #pragma unroll
         for (int t = 0; t < PER; ++t) {
             const int k = g * PER + t;
-            x[t] = (k < K && c < cw) ? B[k * CH + c] : 0.0f;
+            x[t] = (k < K && c < cwh) ? B[k * CH + cb + c] : 0.0f;
         }
         const int off = kmajor_off<KIND>(c, g * PER, NB);
         SplitRow<KIND>::store(ts.b_hi + off, ts.b_lo + off, x);
@@ -577,7 +582,7 @@ __device__ void gemm_sub_tc(float *__restrict__ Mg, int LDC, int r0, int r1, int
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (ok) {
             const int row = rb + warp * 32 + lane;
-            float *crow = Mg + (long long)min(row, r1 - 1) * LDC + c0;
+            float *crow = Mg + (long long)min(row, r1 - 1) * LDC + c0 + cb;
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 float v[32];
@@ -586,7 +591,7 @@ __device__ void gemm_sub_tc(float *__restrict__ Mg, int LDC, int r0, int r1, int
 #pragma unroll
                     for (int g = 0; g < 8; ++g) {
                         const int c = half * 32 + g * 4;
-                        if (c < cw) {
+                        if (c < cwh) {
                             float4 cv = *(float4 *)(crow + c);
                             cv.x -= v[g * 4];
                             cv.y -= v[g * 4 + 1];
@@ -604,6 +609,7 @@ __device__ void gemm_sub_tc(float *__restrict__ Mg, int LDC, int r0, int r1, int
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (tid == 0) *ts.phase = phase ^ 1u;
+    }
     }
 }
 
