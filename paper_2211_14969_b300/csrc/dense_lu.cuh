@@ -43,7 +43,6 @@ struct Cfg {
     // 128-column chunks, so a right-hand block of up to 128 columns is one
     // chunk), FP64 16 x 8 (64 x 32)
     static constexpr int TY = sizeof(T) == 4 ? 8 : 16, TX = NT / TY;
-    static constexpr int BM = 2 * TY * HV;  // rows per update pass
     static constexpr int CH = 2 * TX * HV;  // columns per chunk
 };
 
@@ -204,11 +203,13 @@ __device__ __forceinline__ void record_pivot(int j, int pr, const Smem<T> &sm) {
 // interchanges go through a small shared buffer); the rest of the panel is
 // then updated as a block with the sub-panel's L still in registers.
 // Panels taller than RMAX * NT rows use the shared-memory form throughout.
+// Register form for panels of at most R * NT rows (R rows a thread).
+template <typename T, int NB, int R>
+__device__ void panel_factor_reg(T *__restrict__ P, int ldp, int mp, int nbk, int k0, const Smem<T> &sm);
+
 template <typename T, int NB>
 __device__ void panel_factor(T *__restrict__ P, int ldp, int mp, int nbk, int k0, const Smem<T> &sm) {
-    constexpr int W = PanelCfg<T>::W, RMAX = PanelCfg<T>::RMAX;
-    using V = typename Vec<T>::type;
-    constexpr int HV = Vec<T>::N;
+    constexpr int RMAX = PanelCfg<T>::RMAX;
     const int tid = threadIdx.x;
     if (mp > RMAX * NT) {
         for (int j = 0; j < nbk; ++j) {
@@ -246,6 +247,20 @@ __device__ void panel_factor(T *__restrict__ P, int ldp, int mp, int nbk, int k0
         }
         return;
     }
+    // the fewest register rows a thread needs for this panel's height
+    if (mp <= NT) panel_factor_reg<T, NB, 1>(P, ldp, mp, nbk, k0, sm);
+    else if (mp <= 2 * NT) panel_factor_reg<T, NB, 2>(P, ldp, mp, nbk, k0, sm);
+    else if (mp <= 3 * NT) panel_factor_reg<T, NB, 3>(P, ldp, mp, nbk, k0, sm);
+    else if (mp <= 4 * NT) panel_factor_reg<T, NB, 4>(P, ldp, mp, nbk, k0, sm);
+    else if constexpr (RMAX > 4) panel_factor_reg<T, NB, RMAX>(P, ldp, mp, nbk, k0, sm);
+}
+
+template <typename T, int NB, int RMAX>
+__device__ void panel_factor_reg(T *__restrict__ P, int ldp, int mp, int nbk, int k0, const Smem<T> &sm) {
+    constexpr int W = PanelCfg<T>::W;
+    using V = typename Vec<T>::type;
+    constexpr int HV = Vec<T>::N;
+    const int tid = threadIdx.x;
     T *bufA = sm.redv + NWARP;   // pivot row of the sub-panel (W values)
     T *bufB = sm.Us;             // displaced row (W values); Us is idle here
     for (int s0 = 0; s0 < nbk; s0 += W) {
@@ -403,11 +418,15 @@ __device__ __forceinline__ void gemm_sub(T *__restrict__ Mg, int LDC, int r0, in
                                          const T *__restrict__ B, int K) {
     using CF = Cfg<T, NB>;
     using V = typename Vec<T>::type;
-    constexpr int HV = CF::HV, TY = CF::TY, TX = CF::TX, CH = CF::CH;
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int cA = tx * HV, cB = TX * HV + tx * HV;
-    for (int rb = r0; rb < r1; rb += CF::BM) {
-        int sa = rb + ty * HV, sb = rb + TY * HV + ty * HV;
+    constexpr int HV = CF::HV, TX = CF::TX, CH = CF::CH;
+    // threads across the columns: just enough 2HV-column tiles for cw (a
+    // full chunk uses TX of them); the rest of the CTA goes to rows
+    const int txr = min(TX, (cw + 2 * HV - 1) / (2 * HV)), tyr = NT / txr;
+    if (threadIdx.x >= txr * tyr) return;
+    const int tx = threadIdx.x % txr, ty = threadIdx.x / txr;
+    const int cA = tx * HV, cB = txr * HV + tx * HV;
+    for (int rb = r0; rb < r1; rb += 2 * tyr * HV) {
+        int sa = rb + ty * HV, sb = rb + tyr * HV + ty * HV;
         const bool va = sa < r1, vb = sb < r1;
         if (!va && !vb) continue;
         const int ia = (va ? sa : r0) - arow0, ib = (vb ? sb : r0) - arow0;
