@@ -464,6 +464,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const Smem<T> sm = carve<T, NB>(smem_raw, P.blk.ldp);
     const int ldp = P.blk.ldp;
+    constexpr bool INV = use_inverses<T, NB, TCK>();   // diagonal-block inverses kept (FP32 path)
     unsigned char *slot = P.work + (long long)blockIdx.x * P.slot_bytes;
     T *M = (T *)slot;
     tc::TcState tcs{};
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             const long long mbytes = (((long long)L.n * L.LDC * (long long)sizeof(T)) + 255) & ~255LL;
             double *X = (double *)(slot + mbytes);
             int *perm_g = (int *)(X + (long long)L.n * L.r);   // 3 NB ints per panel
-            lu_solve<T, NB, TCK>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm, tsp);
+            lu_solve<T, NB, TCK, INV>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm, tsp);
             float *eta = (float *)(perm_g + 3 * (L.n + 64));
             float *nf = eta + ((L.r + 63) & ~63);                 // 12 floats per interior node
             const float *Dhi = P.dt.dmat32 + P.dt.doff[L.p], *Dlo = P.dt.dmat_lo + P.dt.doff[L.p];
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                 while (!done && it < P.kmax) {
                     residual<T>(M, X, L, Dhi, Dlo, nf, (float2 *)sm.Ps + 2 * L.p * L.p, (float2 *)sm.Ps, xs_cols);
                     __syncthreads();
-                    lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
+                    lu_solve<T, NB, 0, INV>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
                     done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us);
                     ++it;
                 }
@@ -603,7 +604,7 @@ cudaError_t launch_leaf_nodes(const LeafTables &lt, int n_leaves, double *xy, cu
 namespace {
 
 template <typename T, int NB>
-size_t smem_of(int ldp) { return smem_bytes_for<T, NB>(ldp); }
+size_t smem_of(int ldp) { return smem_bytes_for<T, NB>(ldp, use_inverses<T, NB, 0>()); }
 
 template <typename K>
 int occupancy(K kernel, size_t smem) {
@@ -616,7 +617,7 @@ int occupancy(K kernel, size_t smem) {
 template <typename T, int NB, int TCK>
 size_t kernel_smem(int ldp) {
     if constexpr (TCK == 0) return smem_of<T, NB>(ldp);
-    else return tc_smem_offset(smem_of<T, NB>(ldp)) + tc::operand_bytes<TCK>(NB) + 64;
+    else return tc_smem_offset(smem_bytes_for<T, NB>(ldp)) + tc::operand_bytes<TCK>(NB) + 64;
 }
 
 template <typename T, int NB, bool MIXED, int TCK = 0>

@@ -58,12 +58,18 @@ struct Smem {
     int *xdst; // NB
     int *misc; // scalars: [0] leaf, [1] info, [2..] free
     int *map;  // ldp: row permutation scratch
+    T *Ts;     // NB x NB: a triangular inverse with its zeros (FP32 path only)
 };
 
+// Whether an elimination keeps the inverses of its diagonal blocks (FP32
+// CUDA-core path with panels of 16 or 32 columns; see panel_inverses).
+template <typename T, int NB, int TCK>
+__host__ __device__ constexpr bool use_inverses() { return sizeof(T) == 4 && NB >= 16 && TCK == 0; }
+
 template <typename T, int NB>
-__host__ __device__ constexpr size_t smem_bytes_for(int ldp) {
+__host__ __device__ constexpr size_t smem_bytes_for(int ldp, bool with_ts = false) {
     return sizeof(T) * ((size_t)NB * ldp + (size_t)NB * Cfg<T, NB>::CH + NB + 8 + NWARP) +
-           sizeof(int) * (NWARP + 3 * NB + 16 + ldp) + 64;
+           sizeof(int) * (NWARP + 3 * NB + 16 + ldp) + 64 + (with_ts ? sizeof(T) * NB * NB + 16 : 0);
 }
 
 template <typename T, int NB>
@@ -88,6 +94,8 @@ __device__ Smem<T> carve(unsigned char *base, int ldp) {
     s.misc = ip;
     ip += 16;
     s.map = ip;
+    ip += ldp;
+    s.Ts = (T *)(((uintptr_t)ip + 15) & ~(uintptr_t)15);
     return s;
 }
 
@@ -410,6 +418,125 @@ __device__ void panel_permutation(int nbk, const Smem<T> &sm) {
     __syncthreads();
 }
 
+// Inverses of the diagonal block of a factored panel (FP32 path).  The top
+// nbk x nbk block of the shared panel P holds L11 (unit lower, below the
+// diagonal) and U11 (upper, with the pivots); both are replaced in place by
+// their inverses, which then travel to the workspace with the panel.  Every
+// later triangular solve with them (the U12 rows of each update chunk, the
+// back substitution, the refinement replays) becomes a product whose
+// outputs are independent dot products (tri_mul) instead of a chain of nbk
+// dependent steps per column.  Warp 0 forms column j of L11^-1 (thread j),
+// warp 1 column j of U11^-1, each by substitution on e_j; Ts receives
+// L11^-1 with its unit diagonal and zeros written out.  A zero pivot (info
+// already set by panel_factor) gives non-finite inverses.
+template <typename T, int NB>
+__device__ void panel_inverses(T *__restrict__ P, int ldp, int nbk, const Smem<T> &sm) {
+    using V = typename Vec<T>::type;
+    constexpr int HV = Vec<T>::N;
+    static_assert(2 * NB <= NT && (NB & (NB - 1)) == 0, "two warps of NB columns");
+    const int tid = threadIdx.x, j = tid & (NB - 1);
+    const bool lower = tid < NB, upper = tid >= NB && tid < 2 * NB;
+    for (int k = tid; k < nbk; k += NT) sm.redv[k] = T(1) / P[k * ldp + k];
+    __syncthreads();
+    T x[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) x[i] = i == j ? T(1) : T(0);
+    if (lower) {
+        // forward: after step k, x[k + 1] is final (x[i < j] stay 0)
+#pragma unroll
+        for (int k = 0; k < NB - 1; ++k) {
+            const T xk = x[k];
+            const T *col = P + k * ldp;
+#pragma unroll
+            for (int g = (k + 1) / HV; g < NB / HV; ++g) {
+                const V lv = *(const V *)(col + g * HV);
+                const T *pl = (const T *)&lv;
+#pragma unroll
+                for (int t = 0; t < HV; ++t)
+                    if (g * HV + t > k) x[g * HV + t] = fma(-pl[t], xk, x[g * HV + t]);
+            }
+        }
+    } else if (upper) {
+        // backward: x[k] /= U[k][k], then x[i < k] -= U[i][k] x[k]
+#pragma unroll
+        for (int k = NB - 1; k >= 0; --k) {
+            if (k < nbk) {
+                const T xk = x[k] * sm.redv[k];
+                x[k] = xk;
+                const T *col = P + k * ldp;
+#pragma unroll
+                for (int g = 0; g < (k + HV - 1) / HV; ++g) {
+                    const V uv = *(const V *)(col + g * HV);
+                    const T *pu = (const T *)&uv;
+#pragma unroll
+                    for (int t = 0; t < HV; ++t)
+                        if (g * HV + t < k) x[g * HV + t] = fma(-pu[t], xk, x[g * HV + t]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (lower) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            if (i > j && i < nbk) P[j * ldp + i] = x[i];
+            sm.Ts[j * NB + i] = (i < nbk && j < nbk) ? x[i] : T(0);
+        }
+    } else if (upper && j < nbk) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+            if (i <= j) P[j * ldp + i] = x[i];
+    }
+    __syncthreads();
+}
+
+// Rows [0, nbk) x columns [0, cw) of the chunk Us replaced by Ts * Us and
+// also written to rows row0.. (columns c0..) of M.  Ts is NB x NB
+// column-major with its zeros present, so each output is one dot product.
+// Thread tile: 4 rows x NB/4 columns (NB/16 vectors of 4, spread so a
+// warp's vector loads of Us are consecutive).
+template <typename T, int NB>
+__device__ void tri_mul(const Smem<T> &sm, int nbk, int cw, T *__restrict__ M, int LDC, int row0, int c0) {
+    static_assert(sizeof(T) == 4 && NB >= 16, "FP32 path, panels of 16 or 32");
+    constexpr int CH = Cfg<T, NB>::CH, RG = NB / 4, TXC = NT / RG, NV = CH / (4 * TXC);
+    const int tx = threadIdx.x % TXC, ty = threadIdx.x / TXC;
+    float acc[4][4 * NV];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4 * NV; ++v) acc[u][v] = 0.0f;
+#pragma unroll 4
+    for (int k = 0; k < nbk; ++k) {
+        const float4 a = *(const float4 *)(sm.Ts + k * NB + ty * 4);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float4 b = *(const float4 *)(sm.Us + k * CH + v * 4 * TXC + tx * 4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc[u][4 * v] = fmaf(av[u], b.x, acc[u][4 * v]);
+                acc[u][4 * v + 1] = fmaf(av[u], b.y, acc[u][4 * v + 1]);
+                acc[u][4 * v + 2] = fmaf(av[u], b.z, acc[u][4 * v + 2]);
+                acc[u][4 * v + 3] = fmaf(av[u], b.w, acc[u][4 * v + 3]);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = ty * 4 + u;
+        if (i >= nbk) continue;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int c = v * 4 * TXC + tx * 4;
+            if (c >= cw) continue;   // a vector that starts inside cw may end in the row padding
+            const float4 o = make_float4(acc[u][4 * v], acc[u][4 * v + 1], acc[u][4 * v + 2], acc[u][4 * v + 3]);
+            *(float4 *)(sm.Us + i * CH + c) = o;
+            *(float4 *)(M + (long long)(row0 + i) * LDC + c0 + c) = o;
+        }
+    }
+}
+
 // Mg[r, c0 + c] -= sum_kk A[kk*lda + r - arow0] * B[kk*CH + c] for rows
 // [r0, r1), columns [0, cw).  A and B in shared memory.
 template <typename T, int NB>
@@ -634,7 +761,7 @@ __device__ void gemm_sub_tc(float *__restrict__ Mg, int LDC, int r0, int r1, int
 
 // Apply the panel at rows k0.. (permutation, unit-lower solve, trailing
 // update) to columns [cstart, C) of M.
-template <typename T, int NB, int TCK = 0>
+template <typename T, int NB, int TCK = 0, bool INV = false>
 __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, int nbk, int cstart, int ldp,
                             const Smem<T> &sm, const tc::TcState *ts = nullptr) {
     using CF = Cfg<T, NB>;
@@ -668,10 +795,12 @@ __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, in
             const int j = e / CH, c = e % CH;
             if (e < nbk * CH && c < cw && sm.xdst[j] >= 0) M[(long long)(k0 + sm.xdst[j]) * LDC + c0 + c] = xv[t];
         }
-        // unit-lower solve, one column per thread, column in registers;
+        // unit-lower solve: with the inverse kept in Ts, one product;
+        // otherwise one column per thread, column in registers,
         // column-oriented (axpy) so each step's multipliers L[j+1.., j] are
         // consecutive in the shared panel and load as 16-byte vectors
-        for (int c = tid; c < cw; c += NT) {
+        if constexpr (INV) tri_mul<T, NB>(sm, nbk, cw, M, LDC, k0, c0);
+        else for (int c = tid; c < cw; c += NT) {
             T u[NB];
 #pragma unroll
             for (int j = 0; j < NB; ++j) u[j] = j < nbk ? sm.Us[j * CH + c] : T(0);
@@ -714,7 +843,7 @@ __device__ void apply_panel(T *__restrict__ M, int LDC, int n, int C, int k0, in
 // perm_g is given, factoring stores each panel's permutation there (3 NB
 // ints per panel: top-row sources, displaced sources, displaced targets)
 // and replaying (factor = false) reads it back.
-template <typename T, int NB, int TCK = 0>
+template <typename T, int NB, int TCK = 0, bool INV = false>
 __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool factor, int *perm_g, int ldp,
                          const Smem<T> &sm, const tc::TcState *ts = nullptr) {
     using CF = Cfg<T, NB>;
@@ -734,8 +863,18 @@ __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool 
             }
         stage<T, true>(M + (long long)k0 * LDC + k0, LDC, sm.Ps, ldp, mp, nbk);
         __syncthreads();
+        if constexpr (INV) {
+            if (!factor) {   // L11^-1 from the stored panel, zeros and unit diagonal written out
+                for (int e = tid; e < NB * NB; e += NT) {
+                    const int k = e / NB, i = e - k * NB;
+                    sm.Ts[e] = (i < nbk && k < nbk) ? (i > k ? sm.Ps[k * ldp + i] : (i == k ? T(1) : T(0))) : T(0);
+                }
+                __syncthreads();
+            }
+        }
         if (factor) {
             panel_factor<T, NB>(sm.Ps, ldp, mp, nbk, k0, sm);
+            if constexpr (INV) panel_inverses<T, NB>(sm.Ps, ldp, nbk, sm);
             stage<T, false>(M + (long long)k0 * LDC + k0, LDC, sm.Ps, ldp, mp, nbk);
             panel_permutation<T>(nbk, sm);
             if (pg)
@@ -748,7 +887,7 @@ __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool 
         const int cstart = factor ? (k0 + nbk < n ? k0 + nbk : n4) : n4;
         // the factorization's trailing updates go to the tensor cores when
         // enabled; the right-hand-only replays stay on the FP32 pipe
-        apply_panel<T, NB, TCK>(M, LDC, n, C, k0, nbk, cstart, ldp, sm, factor ? ts : nullptr);
+        apply_panel<T, NB, TCK, INV>(M, LDC, n, C, k0, nbk, cstart, ldp, sm, factor ? ts : nullptr);
     }
 
     // U X = Y for the right-hand columns, block rows from the bottom
@@ -756,11 +895,28 @@ __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool 
         const int nbk = min(NB, n - kb0), rows = kb0 + nbk;
         stage<T, true>(M + kb0, LDC, sm.Ps, ldp, rows, nbk);
         __syncthreads();
-        for (int j = tid; j < nbk; j += NT) sm.redv[j] = T(1) / sm.Ps[j * ldp + kb0 + j];
+        if constexpr (INV) {   // U11^-1 of the diagonal block, zeros written out
+            for (int e = tid; e < NB * NB; e += NT) {
+                const int k = e / NB, i = e - k * NB;
+                sm.Ts[e] = (i <= k && k < nbk) ? sm.Ps[k * ldp + kb0 + i] : T(0);
+            }
+        } else {
+            for (int j = tid; j < nbk; j += NT) sm.redv[j] = T(1) / sm.Ps[j * ldp + kb0 + j];
+        }
         __syncthreads();
         for (int c0 = n4; c0 < C; c0 += CH) {
             const int cw = min(CH, C - c0);
-            for (int c = tid; c < cw; c += NT) {
+            if constexpr (INV) {
+                // the block rows of the right-hand side into Us, then X = U11^-1 Y
+                constexpr int VPR = CH / HV;
+                for (int e = tid; e < nbk * VPR; e += NT) {
+                    const int j = e / VPR, c = (e % VPR) * HV;
+                    if (c < cw) cp_async<16>(&sm.Us[j * CH + c], &M[(long long)(kb0 + j) * LDC + c0 + c]);
+                }
+                cp_async_wait();
+                __syncthreads();
+                tri_mul<T, NB>(sm, nbk, cw, M, LDC, kb0, c0);
+            } else for (int c = tid; c < cw; c += NT) {
                 T u[NB];
 #pragma unroll
                 for (int j = 0; j < NB; ++j) u[j] = j < nbk ? M[(long long)(kb0 + j) * LDC + c0 + c] : T(0);
