@@ -236,14 +236,17 @@ __device__ void node_factors(const LeafInfo &L, double kappa2, float *__restrict
 // corners; B is 0 for c < n_b (the -A_ib e_c term is inside A applied to
 // that grid) and f_I otherwise.  Written to M[:, n4 + c] in the working
 // type.
-// Columns go in chunks of cw, staged in shared memory as hi/lo float pairs
-// (Xs, n x cwp, cwp = cw rounded up to 4); D and D^2 are staged as pairs in
-// Dp.  Each thread takes one interior node and 4 columns, so the four sums
-// of a line are independent chains sharing the D loads.
-template <typename T>
+// Columns go in chunks of cw, staged in shared memory as separate hi and lo
+// float planes (Xh, Xl: n x cwp each, cwp = cw rounded up to 4, so a warp's
+// 16-byte loads of consecutive column groups are consecutive); D and D^2 are
+// staged as pairs in Dp.  Each thread takes one interior node and 4 columns;
+// the x-line and y-line sums run in one loop, eight independent chains
+// sharing the loop.  GENERAL adds the first-derivative and mixed terms
+// (leaf_flags != 0); without them those terms are exactly zero and skipped.
+template <typename T, bool GENERAL>
 __device__ void residual(T *__restrict__ M, const double *__restrict__ X, const LeafInfo &L,
                          const float *__restrict__ Dh, const float *__restrict__ Dl,
-                         const float *__restrict__ nf, float2 *__restrict__ Xs, float2 *__restrict__ Dp,
+                         const float *__restrict__ nf, float *__restrict__ Xs, float2 *__restrict__ Dp,
                          int cw_max) {
     constexpr int G = 4;
     const int p = L.p, q = L.q, r = L.r, nbd = L.nbd, n = L.n, p2 = p * p;
@@ -251,56 +254,54 @@ __device__ void residual(T *__restrict__ M, const double *__restrict__ X, const 
     const float2 *Dq = Dp, *D2q = Dp + p2;
     for (int c0 = 0; c0 < r; c0 += cw_max) {
         const int cw = min(cw_max, r - c0), cwp = (cw + 3) & ~3, ng = cwp / G;
+        float *Xh = Xs, *Xl = Xs + (long long)n * cwp;
         for (int e = threadIdx.x; e < n * cwp; e += NT) {
             const int i = e / cwp, cc = e - i * cwp;
             DF d = {0.0f, 0.0f};
             if (cc < cw) d = df_from(X[(long long)i * r + c0 + cc]);
-            Xs[e] = make_float2(d.hi, d.lo);
+            Xh[e] = d.hi;
+            Xl[e] = d.lo;
         }
         __syncthreads();
         for (int w = threadIdx.x; w < n * ng; w += NT) {
             const int rr = w / ng, g = w - rr * ng;
             const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
-            DF ax2[G], ax1[G], ay2[G], ay1[G], axy[G];
+            DF ax2[G], ay2[G], ax1[G], ay1[G], axy[G];
 #pragma unroll
-            for (int t = 0; t < G; ++t) ax2[t] = ax1[t] = ay2[t] = ay1[t] = axy[t] = DF{0.0f, 0.0f};
-            // x-line interior: nodes (k, j), k = 1..q, stride q rows of Xs
+            for (int t = 0; t < G; ++t) ax2[t] = ay2[t] = ax1[t] = ay1[t] = axy[t] = DF{0.0f, 0.0f};
+            // x-line interior: nodes (k, j), k = 1..q, stride q rows;
+            // y-line interior: nodes (i, l), l = 1..q, consecutive rows
             {
-                const float4 *xp = (const float4 *)(Xs + (j - 1) * cwp + g * G);
-                const int stride = q * cwp / 2;   // in float4 units (two pairs each)
-                for (int k = 1; k <= q; ++k, xp += stride) {
-                    const float4 u01 = xp[0], u23 = xp[1];
-                    const float2 d2 = D2q[i * p + k];
-                    df_mac(ax2[0], d2.x, d2.y, u01.x, u01.y);
-                    df_mac(ax2[1], d2.x, d2.y, u01.z, u01.w);
-                    df_mac(ax2[2], d2.x, d2.y, u23.x, u23.y);
-                    df_mac(ax2[3], d2.x, d2.y, u23.z, u23.w);
-                    if (L.flags & 2) {
-                        const float2 d1 = Dq[i * p + k];
-                        df_mac(ax1[0], d1.x, d1.y, u01.x, u01.y);
-                        df_mac(ax1[1], d1.x, d1.y, u01.z, u01.w);
-                        df_mac(ax1[2], d1.x, d1.y, u23.x, u23.y);
-                        df_mac(ax1[3], d1.x, d1.y, u23.z, u23.w);
-                    }
-                }
-            }
-            // y-line interior: nodes (i, l), l = 1..q, consecutive rows of Xs
-            {
-                const float4 *xp = (const float4 *)(Xs + (i - 1) * q * cwp + g * G);
-                const int stride = cwp / 2;
-                for (int l = 1; l <= q; ++l, xp += stride) {
-                    const float4 u01 = xp[0], u23 = xp[1];
-                    const float2 d2 = D2q[j * p + l];
-                    df_mac(ay2[0], d2.x, d2.y, u01.x, u01.y);
-                    df_mac(ay2[1], d2.x, d2.y, u01.z, u01.w);
-                    df_mac(ay2[2], d2.x, d2.y, u23.x, u23.y);
-                    df_mac(ay2[3], d2.x, d2.y, u23.z, u23.w);
-                    if (L.flags & 4) {
-                        const float2 d1 = Dq[j * p + l];
-                        df_mac(ay1[0], d1.x, d1.y, u01.x, u01.y);
-                        df_mac(ay1[1], d1.x, d1.y, u01.z, u01.w);
-                        df_mac(ay1[2], d1.x, d1.y, u23.x, u23.y);
-                        df_mac(ay1[3], d1.x, d1.y, u23.z, u23.w);
+                const float *px = Xh + (j - 1) * cwp + g * G, *py = Xh + (i - 1) * q * cwp + g * G;
+                const long long lo = (long long)n * cwp;
+                const int sx = q * cwp, sy = cwp;
+                for (int k = 1; k <= q; ++k, px += sx, py += sy) {
+                    const float4 xh = *(const float4 *)px, xl = *(const float4 *)(px + lo);
+                    const float4 yh = *(const float4 *)py, yl = *(const float4 *)(py + lo);
+                    const float2 dx = D2q[i * p + k], dy = D2q[j * p + k];
+                    df_mac(ax2[0], dx.x, dx.y, xh.x, xl.x);
+                    df_mac(ay2[0], dy.x, dy.y, yh.x, yl.x);
+                    df_mac(ax2[1], dx.x, dx.y, xh.y, xl.y);
+                    df_mac(ay2[1], dy.x, dy.y, yh.y, yl.y);
+                    df_mac(ax2[2], dx.x, dx.y, xh.z, xl.z);
+                    df_mac(ay2[2], dy.x, dy.y, yh.z, yl.z);
+                    df_mac(ax2[3], dx.x, dx.y, xh.w, xl.w);
+                    df_mac(ay2[3], dy.x, dy.y, yh.w, yl.w);
+                    if constexpr (GENERAL) {
+                        if (L.flags & 2) {
+                            const float2 d1 = Dq[i * p + k];
+                            df_mac(ax1[0], d1.x, d1.y, xh.x, xl.x);
+                            df_mac(ax1[1], d1.x, d1.y, xh.y, xl.y);
+                            df_mac(ax1[2], d1.x, d1.y, xh.z, xl.z);
+                            df_mac(ax1[3], d1.x, d1.y, xh.w, xl.w);
+                        }
+                        if (L.flags & 4) {
+                            const float2 d1 = Dq[j * p + k];
+                            df_mac(ay1[0], d1.x, d1.y, yh.x, yl.x);
+                            df_mac(ay1[1], d1.x, d1.y, yh.y, yl.y);
+                            df_mac(ay1[2], d1.x, d1.y, yh.z, yl.z);
+                            df_mac(ay1[3], d1.x, d1.y, yh.w, yl.w);
+                        }
                     }
                 }
             }
@@ -315,47 +316,55 @@ __device__ void residual(T *__restrict__ M, const double *__restrict__ X, const 
                 if (c == es) { df_mac(ay2[t], D2q[j * p].x, D2q[j * p].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p].x, Dq[j * p].y, 1.0f, 0.0f); }
                 if (c == en) { df_mac(ay2[t], D2q[j * p + p - 1].x, D2q[j * p + p - 1].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p + p - 1].x, Dq[j * p + p - 1].y, 1.0f, 0.0f); }
             }
-            if (L.flags & 1) {   // mixed derivative: every node of the leaf
+            if constexpr (GENERAL) {
+                if (L.flags & 1) {   // mixed derivative: every node of the leaf
 #pragma unroll
-                for (int t = 0; t < G; ++t) {
-                    const int cc = g * G + t, c = c0 + cc;
-                    if (cc >= cw) continue;
-                    auto U = [&](int k, int l) -> float2 {
-                        if (k >= 1 && k <= q && l >= 1 && l <= q) return Xs[((k - 1) * q + (l - 1)) * cwp + cc];
-                        if (c >= nbd || ((k == 0 || k == p - 1) && (l == 0 || l == p - 1))) return make_float2(0.0f, 0.0f);
-                        return make_float2(edge_index(k, l, p, q) == c ? 1.0f : 0.0f, 0.0f);
-                    };
-                    for (int k = 0; k < p; ++k) {
-                        DF sk = {0.0f, 0.0f};
-                        for (int l = 0; l < p; ++l) {
-                            const float2 u = U(k, l);
-                            df_mac(sk, Dq[j * p + l].x, Dq[j * p + l].y, u.x, u.y);
+                    for (int t = 0; t < G; ++t) {
+                        const int cc = g * G + t, c = c0 + cc;
+                        if (cc >= cw) continue;
+                        auto U = [&](int k, int l) -> float2 {
+                            if (k >= 1 && k <= q && l >= 1 && l <= q) {
+                                const int e = ((k - 1) * q + (l - 1)) * cwp + cc;
+                                return make_float2(Xh[e], Xl[e]);
+                            }
+                            if (c >= nbd || ((k == 0 || k == p - 1) && (l == 0 || l == p - 1))) return make_float2(0.0f, 0.0f);
+                            return make_float2(edge_index(k, l, p, q) == c ? 1.0f : 0.0f, 0.0f);
+                        };
+                        for (int k = 0; k < p; ++k) {
+                            DF sk = {0.0f, 0.0f};
+                            for (int l = 0; l < p; ++l) {
+                                const float2 u = U(k, l);
+                                df_mac(sk, Dq[j * p + l].x, Dq[j * p + l].y, u.x, u.y);
+                            }
+                            sk = df_norm(sk);
+                            df_mac(axy[t], Dq[i * p + k].x, Dq[i * p + k].y, sk.hi, sk.lo);
                         }
-                        sk = df_norm(sk);
-                        df_mac(axy[t], Dq[i * p + k].x, Dq[i * p + k].y, sk.hi, sk.lo);
                     }
                 }
             }
             // A u = -(a2x ux2 + a1x ux1 + a2y uy2 + a1y uy1 + axy uxy) - dg u_ij;
             // R = B - A u with B = f for load columns
             const float *f6 = nf + rr * 12;
-            const float4 *xij = (const float4 *)(Xs + rr * cwp + g * G);
-            const float4 u01 = xij[0], u23 = xij[1];
-            const float2 uij[G] = {make_float2(u01.x, u01.y), make_float2(u01.z, u01.w), make_float2(u23.x, u23.y),
-                                   make_float2(u23.z, u23.w)};
+            const float4 uh = *(const float4 *)(Xh + rr * cwp + g * G), ul = *(const float4 *)(Xl + rr * cwp + g * G);
+            const float uhv[G] = {uh.x, uh.y, uh.z, uh.w}, ulv[G] = {ul.x, ul.y, ul.z, ul.w};
 #pragma unroll
             for (int t = 0; t < G; ++t) {
                 const int cc = g * G + t, c = c0 + cc;
                 if (cc >= cw) continue;
                 DF au = {0.0f, 0.0f};
-                const DF t0 = df_norm(ax2[t]), t1 = df_norm(ax1[t]), t2 = df_norm(ay2[t]), t3 = df_norm(ay1[t]),
-                         t4 = df_norm(axy[t]);
+                const DF t0 = df_norm(ax2[t]), t2 = df_norm(ay2[t]);
                 df_mac(au, f6[0], f6[1], t0.hi, t0.lo);
-                df_mac(au, f6[2], f6[3], t1.hi, t1.lo);
+                if constexpr (GENERAL) {
+                    const DF t1 = df_norm(ax1[t]);
+                    df_mac(au, f6[2], f6[3], t1.hi, t1.lo);
+                }
                 df_mac(au, f6[4], f6[5], t2.hi, t2.lo);
-                df_mac(au, f6[6], f6[7], t3.hi, t3.lo);
-                df_mac(au, f6[8], f6[9], t4.hi, t4.lo);
-                df_mac(au, f6[10], f6[11], uij[t].x, uij[t].y);
+                if constexpr (GENERAL) {
+                    const DF t3 = df_norm(ay1[t]), t4 = df_norm(axy[t]);
+                    df_mac(au, f6[6], f6[7], t3.hi, t3.lo);
+                    df_mac(au, f6[8], f6[9], t4.hi, t4.lo);
+                }
+                df_mac(au, f6[10], f6[11], uhv[t], ulv[t]);
                 if (c >= nbd && L.f) {
                     const DF b = df_from(L.f[(long long)node * L.m + (c - nbd)]);
                     float s2, se;
@@ -534,7 +543,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                 int it = 0;
                 bool done = false;
                 while (!done && it < P.kmax) {
-                    residual<T>(M, X, L, Dhi, Dlo, nf, (float2 *)sm.Ps + 2 * L.p * L.p, (float2 *)sm.Ps, xs_cols);
+                    float *xs = (float *)((float2 *)sm.Ps + 2 * L.p * L.p);
+                    if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
+                    else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
                     __syncthreads();
                     lu_solve<T, NB, 0, INV>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
                     done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us);
