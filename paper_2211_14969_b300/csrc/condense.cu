@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const Smem<T> sm = carve<T, NB>(smem_raw, P.blk.ldp);
     const int ldp = P.blk.ldp;
-    constexpr bool INV = use_inverses<T, NB, TCK>();   // diagonal-block inverses kept (FP32 path)
+    constexpr bool INV = use_inverses<T, NB, TCK>();   // L11 inverses kept (FP32 path)
     unsigned char *slot = P.work + (long long)blockIdx.x * P.slot_bytes;
     T *M = (T *)slot;
     tc::TcState tcs{};

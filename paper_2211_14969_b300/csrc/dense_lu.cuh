@@ -58,10 +58,10 @@ struct Smem {
     int *xdst; // NB
     int *misc; // scalars: [0] leaf, [1] info, [2..] free
     int *map;  // ldp: row permutation scratch
-    T *Ts;     // NB x NB: a triangular inverse with its zeros (FP32 path only)
+    T *Ts;     // NB x NB: L11^-1 with its zeros and unit diagonal (FP32 path only)
 };
 
-// Whether an elimination keeps the inverses of its diagonal blocks (FP32
+// Whether an elimination keeps the inverses of its unit-lower diagonal blocks (FP32
 // CUDA-core path with panels of 16 or 32 columns; see panel_inverses).
 template <typename T, int NB, int TCK>
 __host__ __device__ constexpr bool use_inverses() { return sizeof(T) == 4 && NB >= 16 && TCK == 0; }
@@ -418,30 +418,27 @@ __device__ void panel_permutation(int nbk, const Smem<T> &sm) {
     __syncthreads();
 }
 
-// Inverses of the diagonal block of a factored panel (FP32 path).  The top
-// nbk x nbk block of the shared panel P holds L11 (unit lower, below the
-// diagonal) and U11 (upper, with the pivots); both are replaced in place by
-// their inverses, which then travel to the workspace with the panel.  Every
-// later triangular solve with them (the U12 rows of each update chunk, the
-// back substitution, the refinement replays) becomes a product whose
-// outputs are independent dot products (tri_mul) instead of a chain of nbk
-// dependent steps per column.  Warp 0 forms column j of L11^-1 (thread j),
-// warp 1 column j of U11^-1, each by substitution on e_j; Ts receives
-// L11^-1 with its unit diagonal and zeros written out.  A zero pivot (info
-// already set by panel_factor) gives non-finite inverses.
+// Inverse of the unit-lower diagonal block of a factored panel (FP32 path).
+// The top nbk x nbk block of the shared panel P holds L11 below its
+// diagonal; it is replaced in place by L11^-1 (also unit lower), which then
+// travels to the workspace with the panel.  The U12 rows of every update
+// chunk, in the factorization and in the refinement replays, are then one
+// product whose outputs are independent dot products (tri_mul) instead of
+// a chain of nbk dependent steps per column.  With partial pivoting
+// |L11| <= 1 and its inverse stays well scaled; U11, which carries the
+// conditioning of the leaf, keeps its substitution in the back solve.
+// Warp 0 forms column j of L11^-1 (thread j) by substitution on e_j; Ts
+// receives the inverse with its unit diagonal and zeros written out.
 template <typename T, int NB>
 __device__ void panel_inverses(T *__restrict__ P, int ldp, int nbk, const Smem<T> &sm) {
     using V = typename Vec<T>::type;
     constexpr int HV = Vec<T>::N;
-    static_assert(2 * NB <= NT && (NB & (NB - 1)) == 0, "two warps of NB columns");
-    const int tid = threadIdx.x, j = tid & (NB - 1);
-    const bool lower = tid < NB, upper = tid >= NB && tid < 2 * NB;
-    for (int k = tid; k < nbk; k += NT) sm.redv[k] = T(1) / P[k * ldp + k];
-    __syncthreads();
+    static_assert(NB <= 32, "one warp of NB columns");
+    const int j = threadIdx.x;
     T x[NB];
+    if (j < NB) {
 #pragma unroll
-    for (int i = 0; i < NB; ++i) x[i] = i == j ? T(1) : T(0);
-    if (lower) {
+        for (int i = 0; i < NB; ++i) x[i] = i == j ? T(1) : T(0);
         // forward: after step k, x[k + 1] is final (x[i < j] stay 0)
 #pragma unroll
         for (int k = 0; k < NB - 1; ++k) {
@@ -456,36 +453,14 @@ __device__ void panel_inverses(T *__restrict__ P, int ldp, int nbk, const Smem<T
                     if (g * HV + t > k) x[g * HV + t] = fma(-pl[t], xk, x[g * HV + t]);
             }
         }
-    } else if (upper) {
-        // backward: x[k] /= U[k][k], then x[i < k] -= U[i][k] x[k]
-#pragma unroll
-        for (int k = NB - 1; k >= 0; --k) {
-            if (k < nbk) {
-                const T xk = x[k] * sm.redv[k];
-                x[k] = xk;
-                const T *col = P + k * ldp;
-#pragma unroll
-                for (int g = 0; g < (k + HV - 1) / HV; ++g) {
-                    const V uv = *(const V *)(col + g * HV);
-                    const T *pu = (const T *)&uv;
-#pragma unroll
-                    for (int t = 0; t < HV; ++t)
-                        if (g * HV + t < k) x[g * HV + t] = fma(-pu[t], xk, x[g * HV + t]);
-                }
-            }
-        }
     }
     __syncthreads();
-    if (lower) {
+    if (j < NB) {
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             if (i > j && i < nbk) P[j * ldp + i] = x[i];
             sm.Ts[j * NB + i] = (i < nbk && j < nbk) ? x[i] : T(0);
         }
-    } else if (upper && j < nbk) {
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-            if (i <= j) P[j * ldp + i] = x[i];
     }
     __syncthreads();
 }
@@ -895,28 +870,11 @@ __device__ void lu_solve(T *__restrict__ M, int LDC, int n, int n4, int C, bool 
         const int nbk = min(NB, n - kb0), rows = kb0 + nbk;
         stage<T, true>(M + kb0, LDC, sm.Ps, ldp, rows, nbk);
         __syncthreads();
-        if constexpr (INV) {   // U11^-1 of the diagonal block, zeros written out
-            for (int e = tid; e < NB * NB; e += NT) {
-                const int k = e / NB, i = e - k * NB;
-                sm.Ts[e] = (i <= k && k < nbk) ? sm.Ps[k * ldp + kb0 + i] : T(0);
-            }
-        } else {
-            for (int j = tid; j < nbk; j += NT) sm.redv[j] = T(1) / sm.Ps[j * ldp + kb0 + j];
-        }
+        for (int j = tid; j < nbk; j += NT) sm.redv[j] = T(1) / sm.Ps[j * ldp + kb0 + j];
         __syncthreads();
         for (int c0 = n4; c0 < C; c0 += CH) {
             const int cw = min(CH, C - c0);
-            if constexpr (INV) {
-                // the block rows of the right-hand side into Us, then X = U11^-1 Y
-                constexpr int VPR = CH / HV;
-                for (int e = tid; e < nbk * VPR; e += NT) {
-                    const int j = e / VPR, c = (e % VPR) * HV;
-                    if (c < cw) cp_async<16>(&sm.Us[j * CH + c], &M[(long long)(kb0 + j) * LDC + c0 + c]);
-                }
-                cp_async_wait();
-                __syncthreads();
-                tri_mul<T, NB>(sm, nbk, cw, M, LDC, kb0, c0);
-            } else for (int c = tid; c < cw; c += NT) {
+            for (int c = tid; c < cw; c += NT) {
                 T u[NB];
 #pragma unroll
                 for (int j = 0; j < NB; ++j) u[j] = j < nbk ? M[(long long)(kb0 + j) * LDC + c0 + c] : T(0);
