@@ -114,7 +114,11 @@ __device__ __forceinline__ int edge_index(int k, int l, int p, int q) {
 // one warp per row.  The row is zeroed, then only the nodes that share a
 // grid line with the row's node are written (all nodes when c12 != 0).  The
 // entries are formed in the working precision from per-row factors and the
-// differentiation matrices held in that precision.
+// differentiation matrices held in that precision.  In FP32 the per-row
+// factors are the coefficients (truncated to float on their bit patterns)
+// times per-leaf float scales, which keeps the slow FP64 pipe out of the
+// assembly; the FP32 matrix only drives the corrections, whose residuals
+// use the FP64 factors.
 template <typename T>
 __device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restrict__ Dw, double kappa2) {
     using V = typename Vec<T>::type;
@@ -123,14 +127,34 @@ __device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restri
     const int p = L.p, q = L.q, p2 = p * p, nA = L.n4 + L.nbd;
     const T *D2w = Dw + p2;
     const bool dense = (L.flags & 1) != 0;
+    // per-leaf scales of c11, c1, c22, c2, c12, b
+    const T s11 = (T)(L.sx * L.sx), s1 = (T)L.sx, s22 = (T)(L.sy * L.sy), s2 = (T)L.sy;
+    const T s12 = (T)(2.0 * L.sx * L.sy), sb = (T)kappa2;
+    auto cvt = [](double v) -> T {
+        if constexpr (sizeof(T) == 4) return d2f_trunc(v);
+        else return v;
+    };
     for (int rr = warp; rr < L.n; rr += NWARP) {
         const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
-        const double c11 = L.coef[node], c12 = L.coef[p2 + node], c22 = L.coef[2 * p2 + node];
-        const double c1 = L.coef[3 * p2 + node], c2 = L.coef[4 * p2 + node];
-        const double b = L.coef[5 * p2 + node];
-        const T ax2 = (T)(c11 * L.sx * L.sx), ax1 = (T)(c1 * L.sx);
-        const T ay2 = (T)(c22 * L.sy * L.sy), ay1 = (T)(c2 * L.sy);
-        const T axy = (T)(2.0 * c12 * L.sx * L.sy), dg = (T)(kappa2 * b);
+        T ax2, ax1, ay2, ay1, axy, dg;
+        if constexpr (sizeof(T) == 4) {
+            ax2 = cvt(L.coef[node]) * s11;
+            axy = cvt(L.coef[p2 + node]) * s12;
+            ay2 = cvt(L.coef[2 * p2 + node]) * s22;
+            ax1 = cvt(L.coef[3 * p2 + node]) * s1;
+            ay1 = cvt(L.coef[4 * p2 + node]) * s2;
+            dg = cvt(L.coef[5 * p2 + node]) * sb;
+        } else {
+            const double c11 = L.coef[node], c12 = L.coef[p2 + node], c22 = L.coef[2 * p2 + node];
+            const double c1 = L.coef[3 * p2 + node], c2 = L.coef[4 * p2 + node];
+            const double b = L.coef[5 * p2 + node];
+            ax2 = c11 * L.sx * L.sx;
+            ax1 = c1 * L.sx;
+            ay2 = c22 * L.sy * L.sy;
+            ay1 = c2 * L.sy;
+            axy = 2.0 * c12 * L.sx * L.sy;
+            dg = kappa2 * b;
+        }
         T *row = M + (long long)rr * L.LDC;
         V zero;
         T *zp = (T *)&zero;
@@ -165,7 +189,7 @@ __device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restri
                 for (int l = lane; l < p; l += 32) put(k, l);
         }
         if (L.f)
-            for (int c = lane; c < L.m; c += 32) row[nA + c] = (T)L.f[(long long)node * L.m + c];
+            for (int c = lane; c < L.m; c += 32) row[nA + c] = cvt(L.f[(long long)node * L.m + c]);
     }
 }
 
@@ -230,7 +254,8 @@ __device__ void node_factors(const LeafInfo &L, double kappa2, float *__restrict
     }
 }
 
-// R = B - A_ii X, applied matrix-free in double-float arithmetic: for column
+// R = B - A_ii X (X as double-float pairs), applied matrix-free in
+// double-float arithmetic: for column
 // c the grid function holds X[:, c] at the interior nodes, the unit vector of
 // edge node c (c < n_b) or zero (c >= n_b) on the edges, zero at the
 // corners; B is 0 for c < n_b (the -A_ib e_c term is inside A applied to
@@ -244,7 +269,7 @@ __device__ void node_factors(const LeafInfo &L, double kappa2, float *__restrict
 // sharing the loop.  GENERAL adds the first-derivative and mixed terms
 // (leaf_flags != 0); without them those terms are exactly zero and skipped.
 template <typename T, bool GENERAL>
-__device__ void residual(T *__restrict__ M, const double *__restrict__ X, const LeafInfo &L,
+__device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const LeafInfo &L,
                          const float *__restrict__ Dh, const float *__restrict__ Dl,
                          const float *__restrict__ nf, float *__restrict__ Xs, float2 *__restrict__ Dp,
                          int cw_max) {
@@ -257,10 +282,10 @@ __device__ void residual(T *__restrict__ M, const double *__restrict__ X, const 
         float *Xh = Xs, *Xl = Xs + (long long)n * cwp;
         for (int e = threadIdx.x; e < n * cwp; e += NT) {
             const int i = e / cwp, cc = e - i * cwp;
-            DF d = {0.0f, 0.0f};
-            if (cc < cw) d = df_from(X[(long long)i * r + c0 + cc]);
-            Xh[e] = d.hi;
-            Xl[e] = d.lo;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (cc < cw) v = X[(long long)i * r + c0 + cc];
+            Xh[e] = v.x;
+            Xl[e] = v.y;
         }
         __syncthreads();
         for (int w = threadIdx.x; w < n * ng; w += NT) {
@@ -423,13 +448,59 @@ __device__ void write_outputs(const CondenseParams &P, int leaf, const LeafInfo 
     }
 }
 
-// X (FP64, n x r) += correction in M[:, n4..]; returns (block-uniform)
+// The same outputs from the mixed path's iterate X (n x r double-float
+// pairs): the DtN sums run in double-float arithmetic with D split into
+// hi/lo floats (Dh, Dl), so the FP64 pipe only forms the final doubles.
+__device__ void write_outputs_df(const CondenseParams &P, int leaf, const LeafInfo &L,
+                                 const float2 *__restrict__ X, const float *__restrict__ Dh,
+                                 const float *__restrict__ Dl) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = L.q, p = L.p, n = L.n, nbd = L.nbd, m = L.m, r = L.r;
+    double *S = P.S ? P.S + P.lt.o_sb[leaf] : nullptr;
+    double *W = (P.W && m > 0) ? P.W + P.lt.o_ni[leaf] * m : nullptr;
+    for (int i = warp; i < n; i += NWARP) {
+        const float2 *xr = X + (long long)i * r;
+        if (S)
+            for (int b = lane; b < nbd; b += 32) S[(long long)i * nbd + b] = f2d(xr[b].x) + f2d(xr[b].y);
+        if (W)
+            for (int cc = lane; cc < m; cc += 32) W[(long long)i * m + cc] = f2d(xr[nbd + cc].x) + f2d(xr[nbd + cc].y);
+    }
+    double *Tm = P.T + P.lt.o_bb[leaf];
+    double *hm = (m > 0 && P.h) ? P.h + P.lt.o_nb[leaf] * m : nullptr;
+    for (int a = warp; a < nbd; a += NWARP) {
+        const int edge = a / q, s = a - edge * q;
+        const bool far = (edge & 1);              // E or N: derivative row p-1
+        const double scl = (far ? 1.0 : -1.0) * ((edge < 2) ? L.sx : L.sy);
+        const double *Drow = L.D + (far ? (p - 1) * p : 0);
+        const float *Dhr = Dh + (far ? (p - 1) * p : 0), *Dlr = Dl + (far ? (p - 1) * p : 0);
+        const long long base = (edge < 2) ? s : (long long)s * q;
+        const long long step = (edge < 2) ? q : 1;
+        const int opp = (edge ^ 1) * q + s;
+        for (int b = lane; b < r; b += 32) {
+            DF acc = {0.0f, 0.0f};
+            for (int k = 1; k <= q; ++k) {
+                const float2 x = X[(base + (k - 1) * step) * r + b];
+                df_mac(acc, Dhr[k], Dlr[k], x.x, x.y);
+            }
+            double v = (f2d(acc.hi) + f2d(acc.lo)) * scl;
+            if (b < nbd) {
+                if (b == a) v += scl * Drow[far ? p - 1 : 0];
+                if (b == opp) v += scl * Drow[far ? 0 : p - 1];
+                Tm[(long long)a * nbd + b] = v;
+            } else if (hm) {
+                hm[(long long)a * m + (b - nbd)] = v;
+            }
+        }
+    }
+}
+
+// X (n x r double-float pairs) += correction in M[:, n4..]; returns (block-uniform)
 // whether every column's estimated error after this correction is <= tol.
 // eta[c] holds the previous relative correction of column c (1 before the
 // first); the estimate for linearly converging refinement is
 // eta_k^2 / eta_{k-1}, and a column that stopped contracting never passes.
 template <typename T>
-__device__ bool refine_update(T *__restrict__ M, double *__restrict__ X, float *__restrict__ eta,
+__device__ bool refine_update(T *__restrict__ M, float2 *__restrict__ X, float *__restrict__ eta,
                               const LeafInfo &L, double tol, unsigned *colmax) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = L.r;
@@ -440,11 +511,15 @@ __device__ bool refine_update(T *__restrict__ M, double *__restrict__ X, float *
         float dmax = 0.0f, xmax = 0.0f;
         if (c < r) {
             for (int i = warp; i < L.n; i += NWARP) {
-                const T d = M[(long long)i * L.LDC + L.n4 + c];
-                const double x = X[(long long)i * r + c] + f2d((float)d);
-                X[(long long)i * r + c] = x;
-                dmax = fmaxf(dmax, fabsf((float)d));
-                xmax = fmaxf(xmax, fabsf(d2f_trunc(x)));
+                const float d = (float)M[(long long)i * L.LDC + L.n4 + c];
+                const float2 x = X[(long long)i * r + c];
+                float s, e;
+                two_sum(x.x, d, s, e);
+                const float lo = __fadd_rn(x.y, e);
+                const float hi = __fadd_rn(s, lo);   // renormalise: |lo| well below ulp(s)
+                X[(long long)i * r + c] = make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+                dmax = fmaxf(dmax, fabsf(d));
+                xmax = fmaxf(xmax, fabsf(hi));
             }
             // non-negative floats order like their bit patterns; NaN maps high
             atomicMax(&colmax[c], dmax == dmax ? __float_as_uint(dmax) : 0x7f800000u);
@@ -517,7 +592,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             if (threadIdx.x == 0) P.info[leaf] = sm.misc[1];
         } else {
             const long long mbytes = (((long long)L.n * L.LDC * (long long)sizeof(T)) + 255) & ~255LL;
-            double *X = (double *)(slot + mbytes);
+            float2 *X = (float2 *)(slot + mbytes);                // iterate, double-float pairs
             int *perm_g = (int *)(X + (long long)L.n * L.r);   // 3 NB ints per panel
             lu_solve<T, NB, TCK, INV>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm, tsp);
             float *eta = (float *)(perm_g + 3 * (L.n + 64));
@@ -532,7 +607,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             const int xs_cols = xs_cap >= 16 ? 16 : xs_cap >= 8 ? 8 : 4;
             for (int i = threadIdx.x >> 5; i < L.n; i += NWARP)
                 for (int c = threadIdx.x & 31; c < L.r; c += 32)
-                    X[(long long)i * L.r + c] = f2d((float)M[(long long)i * L.LDC + L.n4 + c]);
+                    X[(long long)i * L.r + c] = make_float2((float)M[(long long)i * L.LDC + L.n4 + c], 0.0f);
             for (int c = threadIdx.x; c < L.r; c += NT) eta[c] = 1.0f;
             __syncthreads();
             int status = sm.misc[1];
@@ -569,7 +644,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                 status = sd.misc[1];
                 if (threadIdx.x == 0) atomicAdd(P.fallbacks, 1);
             } else {
-                write_outputs<double>(P, leaf, L, X, L.r);
+                write_outputs_df(P, leaf, L, X, P.dt.dmat32 + P.dt.doff[L.p], P.dt.dmat_lo + P.dt.doff[L.p]);
             }
             __syncthreads();
             if (threadIdx.x == 0) P.info[leaf] = status;

@@ -65,7 +65,10 @@ def test_autotune_picks_a_fitting_width_and_keeps_results(tmp_path):
     torch.cuda.synchronize()
     for k in ("S", "T", "h", "W"):
         a, b = out[k], ref[k]
-        assert float((a - b).norm() / b.norm()) < 1e-11, k
+        # another panel width gives other FP32 factors, so the two refined
+        # results agree to the refinement's accuracy (the mixed path's bar
+        # against the exact solution), not bit for bit
+        assert float((a - b).norm() / b.norm()) < TOL["fp32"], k
     nb2, _ = tune.autotune(plan, coef, f, w.m, prec="fp32", cache_path=cache)   # from the cache
     assert nb2 == nb
     with pytest.raises(hps.HpsError):
