@@ -105,8 +105,11 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
  *            k > 0 exact zero pivot at elimination step k (the leaf's S, T
  *                  hold inf/NaN),
  *            -k    mixed precision: refinement did not reach tol in k steps.
- * prec: HPS_FP64 or HPS_MIXED_FP32 (others return HPS_ERR_ARG for now).
- *       HPS_MIXED_FP32 needs 4(p-2) + m <= 256 for the largest p.
+ * prec: HPS_FP64, or the mixed paths HPS_MIXED_FP32 (FP32 LU on the FP32
+ *       pipe), HPS_MIXED_TF32 / HPS_MIXED_BF16 (the factorization's trailing
+ *       updates on the tensor cores as hi*hi + hi*lo + lo*hi splits); all
+ *       mixed paths refine to the same tolerance and need 4(p-2) + m <= 256
+ *       for the largest p.
  * tol, kmax: iterative refinement with FP64 residuals.  Per right-hand column
  *            let eta_k = max|correction_k| / max|X| (eta_0 = 1); the error
  *            left after correction k is estimated as eta_k^2 / eta_{k-1}
@@ -146,6 +149,33 @@ hps_status hps_merge(hps_plan *plan, int nx, int ny, const double *d_T, const do
  * when the merge had m body loads of zero). */
 hps_status hps_solve(hps_plan *plan, const double *d_g, const double *d_S, const double *d_W,
                      int m, double *d_u, hps_stream stream);
+
+/* Leaf solve by re-forming and re-factoring: the paper stores no leaf
+ * factorization; after the reduced system is solved it assembles and
+ * factors every leaf's interior block again and solves for the interior
+ * values (Section 2, the remark on leaf factorizations; Section 4, the leaf
+ * solve after the reduced solve).  For every leaf, with its edge values
+ * u_b given:
+ *   u_i = A_ii^{-1} (f_I - A_ib u_b)      (n_i x m)
+ * one elimination with m right-hand columns (not the 4(p-2) + m of
+ * hps_condense), FP64 or mixed (FP32 factors and the same refinement and
+ * FP64 fallback as hps_condense; HPS_MIXED_TF32 / BF16 run the FP32 path).
+ * Inputs:  d_coef, d_f as for hps_condense (d_f NULL: no body load);
+ *          d_ub per leaf [n_b][m] edge values in the [W, E, S, N] order,
+ *          packed like h.
+ * Outputs: d_u per leaf [p*p][m] at every node (edge nodes copied from
+ *          d_ub, corners 0), packed like the body loads; d_info per leaf
+ *          with the codes of hps_condense.
+ * m >= 1.  The mixed paths need 4(p-2) + m <= 256 for the largest p. */
+hps_status hps_leaf_resolve(hps_plan *plan, hps_prec prec, const double *d_coef, const double *d_f, int m,
+                            const double *d_ub, double tol, int kmax, double *d_u, int *d_info,
+                            hps_stream stream);
+
+/* The stored-operator leaf solve it replaces: u_i = S u_b + W per leaf,
+ * from the S (required) and W (NULL: no body load) of hps_condense, in FP64;
+ * d_ub and d_u as for hps_leaf_resolve; leaves of any orders. */
+hps_status hps_leaf_recover(hps_plan *plan, const double *d_S, const double *d_W, int m, const double *d_ub,
+                            double *d_u, hps_stream stream);
 
 /* Panel width of the blocked LU for one precision path of this plan:
  * nb_panel = 0 restores the automatic choice (the widest panel whose shared

@@ -182,6 +182,29 @@ def leaf_interior_solve(S, W, u_b):
     return S @ u_b + (0.0 if W is None else W)
 
 
+def leaf_resolve(p, box, coef, kappa, u_b, f=None):
+    """Leaf solve by re-forming the leaf system (Section 2 Remark: the leaf
+    factorizations are not kept but formed again after the reduced solve;
+    Section 4: the leaf systems are re-factorized to obtain the solution on
+    the full grid).  The interior values are the solution of
+        A_ii u_i = f_I - A_ib u_b
+    by a plain dense solve.  u_b: edge values (n_b x m, [W, E, S, N]); f: the
+    body load at the p*p nodes (p*p x m) or None.  Returns u at all p*p nodes
+    (p*p x m): interior from the solve, edges from u_b, corners 0 (they are
+    not unknowns)."""
+    A, _, _, _ = leaf_operator(p, box, coef, kappa)
+    ix = leaf_index_sets(p)
+    I, B = ix["I"], ix["B"]
+    u_b = np.asarray(u_b, dtype=np.float64).reshape(len(B), -1)
+    rhs = -A[np.ix_(I, B)] @ u_b
+    if f is not None:
+        rhs = rhs + np.asarray(f, dtype=np.float64).reshape(p * p, -1)[I]
+    u = np.zeros((p * p, u_b.shape[1]))
+    u[I] = np.linalg.solve(A[np.ix_(I, I)], rhs)
+    u[B] = u_b
+    return u
+
+
 # ----------------------------------------------------------------------------
 # Uniform grids of leaves: edge-node keys, merges and the downward solve
 # ----------------------------------------------------------------------------

@@ -18,8 +18,10 @@
 //                   the stored FP32 factors, and X is kept in FP64.  S, T, W
 //                   and h are written from the FP64 iterate.
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include "hps_internal.cuh"
+
 #include "dense_lu.cuh"
 
 namespace hps {
@@ -193,6 +195,49 @@ __device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restri
     }
 }
 
+// Leaf solve: the right-hand sides f_I - A_ib u_b (M holds -A_ib from
+// column n4 and f_I after it), moved to columns [n4, n4 + m); one warp per
+// row, lanes over the columns.  Without the mixed term a row of A_ib has
+// entries only at the four edge nodes on the row's two grid lines.
+template <typename T>
+__device__ void combine_rhs(T *__restrict__ M, const LeafInfo &L, const double *__restrict__ ub) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = L.q, nbd = L.nbd, m = L.m, n4 = L.n4;
+    const bool dense = (L.flags & 1) != 0;
+    auto cvt = [](double v) -> T {
+        if constexpr (sizeof(T) == 4) return d2f_trunc(v);
+        else return v;
+    };
+    constexpr int MAXV = 8;   // m <= 256
+    for (int rr = warp; rr < L.n; rr += NWARP) {
+        const int i = rr / q + 1, j = rr - (i - 1) * q + 1;
+        const int e4[4] = {j - 1, q + j - 1, 2 * q + i - 1, 3 * q + i - 1};   // W, E, S, N
+        T *row = M + (long long)rr * L.LDC;
+        T v[MAXV];
+#pragma unroll
+        for (int t = 0; t < MAXV; ++t) {
+            const int c = lane + 32 * t;
+            v[t] = T(0);
+            if (c < m) {
+                T acc = row[n4 + nbd + c];
+                if (dense) {
+                    for (int e = 0; e < nbd; ++e) acc = fma(row[n4 + e], cvt(ub[(long long)e * m + c]), acc);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc = fma(row[n4 + e4[k]], cvt(ub[(long long)e4[k] * m + c]), acc);
+                }
+                v[t] = acc;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < MAXV; ++t) {
+            const int c = lane + 32 * t;
+            if (c < m) row[n4 + c] = v[t];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Double-float arithmetic (a value carried as an unevaluated sum hi + lo of
 // two floats), built from the error-free transformations TwoSum (Knuth) and
@@ -268,11 +313,11 @@ __device__ void node_factors(const LeafInfo &L, double kappa2, float *__restrict
 // the x-line and y-line sums run in one loop, eight independent chains
 // sharing the loop.  GENERAL adds the first-derivative and mixed terms
 // (leaf_flags != 0); without them those terms are exactly zero and skipped.
-template <typename T, bool GENERAL>
+template <typename T, bool GENERAL, bool RESOLVE = false>
 __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const LeafInfo &L,
                          const float *__restrict__ Dh, const float *__restrict__ Dl,
                          const float *__restrict__ nf, float *__restrict__ Xs, float2 *__restrict__ Dp,
-                         int cw_max) {
+                         int cw_max, const double *__restrict__ ub = nullptr) {
     constexpr int G = 4;
     const int p = L.p, q = L.q, r = L.r, nbd = L.nbd, n = L.n, p2 = p * p;
     for (int e = threadIdx.x; e < 2 * p2; e += NT) Dp[e] = make_float2(Dh[e], Dl[e]);
@@ -331,15 +376,34 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                 }
             }
             // edge nodes on the two lines carry the unit value of their column
+            // (condensation) or the leaf's edge data (leaf solve)
             const int ew = j - 1, ee = q + j - 1, es = 2 * q + i - 1, en = 3 * q + i - 1;
+            if constexpr (RESOLVE) {
 #pragma unroll
-            for (int t = 0; t < G; ++t) {
-                const int c = c0 + g * G + t;
-                if (c >= nbd) continue;
-                if (c == ew) { df_mac(ax2[t], D2q[i * p].x, D2q[i * p].y, 1.0f, 0.0f); df_mac(ax1[t], Dq[i * p].x, Dq[i * p].y, 1.0f, 0.0f); }
-                if (c == ee) { df_mac(ax2[t], D2q[i * p + p - 1].x, D2q[i * p + p - 1].y, 1.0f, 0.0f); df_mac(ax1[t], Dq[i * p + p - 1].x, Dq[i * p + p - 1].y, 1.0f, 0.0f); }
-                if (c == es) { df_mac(ay2[t], D2q[j * p].x, D2q[j * p].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p].x, Dq[j * p].y, 1.0f, 0.0f); }
-                if (c == en) { df_mac(ay2[t], D2q[j * p + p - 1].x, D2q[j * p + p - 1].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p + p - 1].x, Dq[j * p + p - 1].y, 1.0f, 0.0f); }
+                for (int t = 0; t < G; ++t) {
+                    const int c = c0 + g * G + t;
+                    if (g * G + t >= cw) continue;
+                    const DF uw = df_from(ub[(long long)ew * L.m + c]), ue = df_from(ub[(long long)ee * L.m + c]);
+                    const DF us = df_from(ub[(long long)es * L.m + c]), un = df_from(ub[(long long)en * L.m + c]);
+                    df_mac(ax2[t], D2q[i * p].x, D2q[i * p].y, uw.hi, uw.lo);
+                    df_mac(ax2[t], D2q[i * p + p - 1].x, D2q[i * p + p - 1].y, ue.hi, ue.lo);
+                    df_mac(ay2[t], D2q[j * p].x, D2q[j * p].y, us.hi, us.lo);
+                    df_mac(ay2[t], D2q[j * p + p - 1].x, D2q[j * p + p - 1].y, un.hi, un.lo);
+                    df_mac(ax1[t], Dq[i * p].x, Dq[i * p].y, uw.hi, uw.lo);
+                    df_mac(ax1[t], Dq[i * p + p - 1].x, Dq[i * p + p - 1].y, ue.hi, ue.lo);
+                    df_mac(ay1[t], Dq[j * p].x, Dq[j * p].y, us.hi, us.lo);
+                    df_mac(ay1[t], Dq[j * p + p - 1].x, Dq[j * p + p - 1].y, un.hi, un.lo);
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < G; ++t) {
+                    const int c = c0 + g * G + t;
+                    if (c >= nbd) continue;
+                    if (c == ew) { df_mac(ax2[t], D2q[i * p].x, D2q[i * p].y, 1.0f, 0.0f); df_mac(ax1[t], Dq[i * p].x, Dq[i * p].y, 1.0f, 0.0f); }
+                    if (c == ee) { df_mac(ax2[t], D2q[i * p + p - 1].x, D2q[i * p + p - 1].y, 1.0f, 0.0f); df_mac(ax1[t], Dq[i * p + p - 1].x, Dq[i * p + p - 1].y, 1.0f, 0.0f); }
+                    if (c == es) { df_mac(ay2[t], D2q[j * p].x, D2q[j * p].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p].x, Dq[j * p].y, 1.0f, 0.0f); }
+                    if (c == en) { df_mac(ay2[t], D2q[j * p + p - 1].x, D2q[j * p + p - 1].y, 1.0f, 0.0f); df_mac(ay1[t], Dq[j * p + p - 1].x, Dq[j * p + p - 1].y, 1.0f, 0.0f); }
+                }
             }
             if constexpr (GENERAL) {
                 if (L.flags & 1) {   // mixed derivative: every node of the leaf
@@ -352,7 +416,12 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                                 const int e = ((k - 1) * q + (l - 1)) * cwp + cc;
                                 return make_float2(Xh[e], Xl[e]);
                             }
-                            if (c >= nbd || ((k == 0 || k == p - 1) && (l == 0 || l == p - 1))) return make_float2(0.0f, 0.0f);
+                            if ((k == 0 || k == p - 1) && (l == 0 || l == p - 1)) return make_float2(0.0f, 0.0f);
+                            if constexpr (RESOLVE) {
+                                const DF e = df_from(ub[(long long)edge_index(k, l, p, q) * L.m + c]);
+                                return make_float2(e.hi, e.lo);
+                            }
+                            if (c >= nbd) return make_float2(0.0f, 0.0f);
                             return make_float2(edge_index(k, l, p, q) == c ? 1.0f : 0.0f, 0.0f);
                         };
                         for (int k = 0; k < p; ++k) {
@@ -390,8 +459,8 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                     df_mac(au, f6[8], f6[9], t4.hi, t4.lo);
                 }
                 df_mac(au, f6[10], f6[11], uhv[t], ulv[t]);
-                if (c >= nbd && L.f) {
-                    const DF b = df_from(L.f[(long long)node * L.m + (c - nbd)]);
+                if ((RESOLVE || c >= nbd) && L.f) {
+                    const DF b = df_from(L.f[(long long)node * L.m + (RESOLVE ? c : c - nbd)]);
                     float s2, se;
                     two_sum(au.hi, b.hi, s2, se);
                     au.hi = s2;
@@ -494,6 +563,29 @@ __device__ void write_outputs_df(const CondenseParams &P, int leaf, const LeafIn
     }
 }
 
+// Leaf solve output: u at every node [p*p][m]: interior nodes from the
+// solution X (FP64 values, ld ldx, or double-float pairs), edge nodes from
+// the given edge values, corners 0 (they are not unknowns).
+template <typename XT>
+__device__ __forceinline__ double x_value(const XT &x) {
+    if constexpr (std::is_same<XT, float2>::value) return f2d(x.x) + f2d(x.y);
+    else return (double)x;
+}
+template <typename XT>
+__device__ void write_u(const CondenseParams &P, int leaf, const LeafInfo &L, const XT *__restrict__ X, int ldx,
+                        const double *__restrict__ ub) {
+    const int p = L.p, q = L.q, m = L.m;
+    double *u = P.u + P.lt.o_p2[leaf] * m;
+    for (int e = threadIdx.x; e < p * p * m; e += NT) {
+        const int node = e / m, c = e - node * m, i = node / p, j = node - i * p;
+        const bool bi = (i == 0 || i == p - 1), bj = (j == 0 || j == p - 1);
+        double v = 0.0;
+        if (bi != bj) v = ub[(long long)edge_index(i, j, p, q) * m + c];
+        else if (!bi) v = x_value(X[(long long)((i - 1) * q + (j - 1)) * ldx + c]);
+        u[e] = v;
+    }
+}
+
 // X (n x r double-float pairs) += correction in M[:, n4..]; returns (block-uniform)
 // whether every column's estimated error after this correction is <= tol.
 // eta[c] holds the previous relative correction of column c (1 before the
@@ -582,12 +674,20 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
         }
         LeafInfo L = leaf_info(P, leaf);
         L.flags = leaf_flags(L);
+        const double *ubl = P.ub ? P.ub + P.lt.o_nb[leaf] * L.m : nullptr;   // leaf solve: edge values
         const T *Dw = (const T *)(sizeof(T) == 4 ? (const void *)P.dt.dmat32 : (const void *)P.dt.dmat) + P.dt.doff[L.p];
         assemble<T>(M, L, Dw, P.kappa2);
         __syncthreads();
+        if (ubl) {   // one right-hand side per load: f_I - A_ib u_b
+            combine_rhs<T>(M, L, ubl);
+            __syncthreads();
+            L.r = L.m;
+            L.C = L.n4 + L.m;
+        }
         if constexpr (!MIXED) {
             lu_solve<T, NB>(M, L.LDC, L.n, L.n4, L.C, true, nullptr, ldp, sm);
-            write_outputs<T>(P, leaf, L, M + L.n4, L.LDC);
+            if (ubl) write_u<T>(P, leaf, L, M + L.n4, L.LDC, ubl);
+            else write_outputs<T>(P, leaf, L, M + L.n4, L.LDC);
             __syncthreads();
             if (threadIdx.x == 0) P.info[leaf] = sm.misc[1];
         } else {
@@ -619,7 +719,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                 bool done = false;
                 while (!done && it < P.kmax) {
                     float *xs = (float *)((float2 *)sm.Ps + 2 * L.p * L.p);
-                    if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
+                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl);
+                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
                     else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
                     __syncthreads();
                     lu_solve<T, NB, 0, INV>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
@@ -639,10 +740,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                 assemble<double>(M64, L, P.dt.dmat + P.dt.doff[L.p], P.kappa2);
                 if (threadIdx.x == 0) sd.misc[1] = 0;
                 __syncthreads();
+                if (ubl) {
+                    combine_rhs<double>(M64, L, ubl);
+                    __syncthreads();
+                }
                 lu_solve<double, NB / 2>(M64, L.LDC, L.n, L.n4, L.C, true, nullptr, ldp, sd);
-                write_outputs<double>(P, leaf, L, M64 + L.n4, L.LDC);
+                if (ubl) write_u<double>(P, leaf, L, M64 + L.n4, L.LDC, ubl);
+                else write_outputs<double>(P, leaf, L, M64 + L.n4, L.LDC);
                 status = sd.misc[1];
                 if (threadIdx.x == 0) atomicAdd(P.fallbacks, 1);
+            } else if (ubl) {
+                write_u<float2>(P, leaf, L, X, L.r, ubl);
             } else {
                 write_outputs_df(P, leaf, L, X, P.dt.dmat32 + P.dt.doff[L.p], P.dt.dmat_lo + P.dt.doff[L.p]);
             }
@@ -665,6 +773,33 @@ __global__ void __launch_bounds__(NT) dense_solve_kernel(double *base, long long
     if (threadIdx.x == 0 && info) info[blockIdx.x] = sm.misc[1];
 }
 
+// u_i = S u_b + W per leaf (the stored-operator leaf solve), leaves of any
+// order: one CTA per leaf, one thread per output node and column.
+__global__ void __launch_bounds__(NT) leaf_recover_all_kernel(LeafTables lt, int m, const double *__restrict__ S,
+                                                             const double *__restrict__ W,
+                                                             const double *__restrict__ ub, double *__restrict__ u) {
+    const int leaf = blockIdx.x, p = lt.p[leaf], q = p - 2, n = q * q, nbd = 4 * q;
+    const double *Sl = S + lt.o_sb[leaf];
+    const double *Wl = W ? W + lt.o_ni[leaf] * m : nullptr;
+    const double *ul = ub + lt.o_nb[leaf] * m;
+    double *uo = u + lt.o_p2[leaf] * m;
+    (void)n;
+    for (int e = threadIdx.x; e < p * p * m; e += NT) {
+        const int node = e / m, c = e - node * m, i = node / p, j = node - i * p;
+        const bool bi = (i == 0 || i == p - 1), bj = (j == 0 || j == p - 1);
+        double v = 0.0;
+        if (bi != bj) {
+            v = ul[(long long)edge_index(i, j, p, q) * m + c];
+        } else if (!bi) {
+            const int r = (i - 1) * q + (j - 1);
+            v = Wl ? Wl[(long long)r * m + c] : 0.0;
+            const double *Sr = Sl + (long long)r * nbd;
+            for (int b = 0; b < nbd; ++b) v = fma(Sr[b], ul[(long long)b * m + c], v);
+        }
+        uo[e] = v;
+    }
+}
+
 // Node coordinates (Section 2 mesh): x0 + (1 - cos(i pi/(p-1))) hx/2.
 __global__ void leaf_nodes_kernel(LeafTables lt, int n_leaves, double *xy) {
     const int leaf = blockIdx.x;
@@ -681,6 +816,12 @@ __global__ void leaf_nodes_kernel(LeafTables lt, int n_leaves, double *xy) {
 }
 
 }  // namespace
+
+cudaError_t launch_leaf_recover_all(const LeafTables &lt, int n_leaves, int m, const double *S, const double *W,
+                                    const double *ub, double *u, cudaStream_t s) {
+    leaf_recover_all_kernel<<<n_leaves, NT, 0, s>>>(lt, m, S, W, ub, u);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_leaf_nodes(const LeafTables &lt, int n_leaves, double *xy, cudaStream_t s) {
     leaf_nodes_kernel<<<n_leaves, 128, 0, s>>>(lt, n_leaves, xy);

@@ -275,17 +275,12 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
     return HPS_OK;
 }
 
-hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const double *d_f, int m,
-                        double tol, int kmax, double *d_S, double *d_T, double *d_h, double *d_W,
-                        int *d_info, hps_stream stream) {
-    if (P == nullptr) return HPS_ERR_ARG;
-    if (prec != HPS_FP64 && prec != HPS_MIXED_FP32 && prec != HPS_MIXED_TF32 && prec != HPS_MIXED_BF16)
-        return P->fail(HPS_ERR_ARG, "hps_condense: unknown precision");
-    if (d_coef == nullptr || d_T == nullptr || d_info == nullptr)
-        return P->fail(HPS_ERR_ARG, "hps_condense: d_coef, d_T and d_info are required");
-    if (m < 0) return P->fail(HPS_ERR_ARG, "hps_condense: m < 0");
-    if (m > 0 && (d_f == nullptr || d_h == nullptr))
-        return P->fail(HPS_ERR_ARG, "hps_condense: m > 0 needs d_f and d_h");
+// The condensation launch, shared by hps_condense and hps_leaf_resolve
+// (d_ub != nullptr: leaf solve, outputs in d_u).  Arguments checked by the
+// callers except the ones both share.
+static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef, const double *d_f, int m,
+                               double tol, int kmax, double *d_S, double *d_T, double *d_h, double *d_W,
+                               int *d_info, const double *d_ub, double *d_u, hps_stream stream) {
     if (prec != HPS_FP64 && (kmax < 0 || !(tol >= 0.0)))
         return P->fail(HPS_ERR_ARG, "hps_condense: kmax < 0 or tol < 0");
     const bool mixed = prec != HPS_FP64;
@@ -342,6 +337,8 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     prm.kmax = kmax;
     prm.fallbacks = P->d_queue + 1;
     prm.fallback = P->fallback;
+    prm.ub = d_ub;
+    prm.u = d_u;
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(int), s);
     P->last_stream = s;
@@ -358,6 +355,48 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
         cudaEventRecord(evp[1], s);
         ++P->n_timed;
     }
+    P->launches = 1;
+    return HPS_OK;
+}
+
+hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const double *d_f, int m,
+                        double tol, int kmax, double *d_S, double *d_T, double *d_h, double *d_W,
+                        int *d_info, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (prec != HPS_FP64 && prec != HPS_MIXED_FP32 && prec != HPS_MIXED_TF32 && prec != HPS_MIXED_BF16)
+        return P->fail(HPS_ERR_ARG, "hps_condense: unknown precision");
+    if (d_coef == nullptr || d_T == nullptr || d_info == nullptr)
+        return P->fail(HPS_ERR_ARG, "hps_condense: d_coef, d_T and d_info are required");
+    if (m < 0) return P->fail(HPS_ERR_ARG, "hps_condense: m < 0");
+    if (m > 0 && (d_f == nullptr || d_h == nullptr))
+        return P->fail(HPS_ERR_ARG, "hps_condense: m > 0 needs d_f and d_h");
+    return run_condense(P, prec, d_coef, d_f, m, tol, kmax, d_S, d_T, d_h, d_W, d_info, nullptr, nullptr, stream);
+}
+
+hps_status hps_leaf_resolve(hps_plan *P, hps_prec prec, const double *d_coef, const double *d_f, int m,
+                            const double *d_ub, double tol, int kmax, double *d_u, int *d_info,
+                            hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (prec != HPS_FP64 && prec != HPS_MIXED_FP32 && prec != HPS_MIXED_TF32 && prec != HPS_MIXED_BF16)
+        return P->fail(HPS_ERR_ARG, "hps_leaf_resolve: unknown precision");
+    if (d_coef == nullptr || d_ub == nullptr || d_u == nullptr || d_info == nullptr)
+        return P->fail(HPS_ERR_ARG, "hps_leaf_resolve: d_coef, d_ub, d_u and d_info are required");
+    if (m < 1) return P->fail(HPS_ERR_ARG, "hps_leaf_resolve: m < 1");
+    if (prec != HPS_FP64) prec = HPS_MIXED_FP32;   // m columns only: the FP32 path
+    return run_condense(P, prec, d_coef, d_f, m, tol, kmax, nullptr, nullptr, nullptr, nullptr, d_info, d_ub, d_u,
+                        stream);
+}
+
+hps_status hps_leaf_recover(hps_plan *P, const double *d_S, const double *d_W, int m, const double *d_ub,
+                            double *d_u, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (d_S == nullptr || d_ub == nullptr || d_u == nullptr)
+        return P->fail(HPS_ERR_ARG, "hps_leaf_recover: d_S, d_ub and d_u are required");
+    if (m < 1) return P->fail(HPS_ERR_ARG, "hps_leaf_recover: m < 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    P->last_stream = s;
+    cudaError_t e = launch_leaf_recover_all(P->leaf_tables(), P->n_leaves, m, d_S, d_W, d_ub, d_u, s);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_leaf_recover: launch");
     P->launches = 1;
     return HPS_OK;
 }

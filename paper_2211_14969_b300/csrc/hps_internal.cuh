@@ -56,6 +56,10 @@ struct CondenseParams {
     double tol;
     int kmax;
     int fallback;          // mixed path: redo non-converged leaves in FP64
+    // leaf solve (hps_leaf_resolve): edge values per leaf [n_b][m] and the
+    // solution at the nodes [p*p][m]; ub == nullptr condenses instead
+    const double *ub;
+    double *u;
 };
 
 // Host-side launchers (condense.cu).
@@ -64,6 +68,8 @@ size_t condense_smem(int prec, const LuBlocking &b);
 int condense_max_ctas_per_sm(int prec, const LuBlocking &b);
 cudaError_t launch_condense(int prec, const CondenseParams &prm, int grid, cudaStream_t s);
 cudaError_t launch_leaf_nodes(const LeafTables &lt, int n_leaves, double *xy, cudaStream_t s);
+cudaError_t launch_leaf_recover_all(const LeafTables &lt, int n_leaves, int m, const double *S, const double *W,
+                                    const double *ub, double *u, cudaStream_t s);
 
 // Batched dense solves [A | 0 | RHS] -> [LU | 0 | X] (one CTA per system),
 // used by the merges: system s at base + s * stride (elements), row-major,

@@ -53,6 +53,8 @@ def load_library():
     L.hps_condense.argtypes = [vp, i, vp, vp, i, d, i, vp, vp, vp, vp, vp, vp]
     L.hps_merge.argtypes = [vp, i, i, vp, vp, i, vp]
     L.hps_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    L.hps_leaf_resolve.argtypes = [vp, i, vp, vp, i, vp, d, i, vp, vp, vp]
+    L.hps_leaf_recover.argtypes = [vp, vp, vp, i, vp, vp, vp]
     L.hps_set_timing.argtypes = [vp, i]
     L.hps_set_blocking.argtypes = [vp, i, i]
     L.hps_set_fp64_fallback.argtypes = [vp, i]
@@ -153,6 +155,12 @@ class Plan:
     def solve(self, g, S, W, m, out=None, stream=None):
         return hps_solve(self, g, S, W, m, out, stream)
 
+    def leaf_resolve(self, coef, ub, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, out=None, stream=None):
+        return hps_leaf_resolve(self, coef, ub, f, m, prec, tol, kmax, out, stream)
+
+    def leaf_recover(self, S, W, ub, m, out=None, stream=None):
+        return hps_leaf_recover(self, S, W, ub, m, out, stream)
+
     def set_blocking(self, prec, nb_panel):
         """Force the LU panel width of one precision path (0 = automatic)."""
         prec_id = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -246,6 +254,43 @@ def hps_merge(plan, nx, ny, T, h, m, stream=None):
     _check_dev(T, "T", int(plan.layout.o_bb[-1]))
     status = load_library().hps_merge(plan.handle, int(nx), int(ny), _ptr(T), _ptr(h), int(m), _stream(stream))
     plan.check(status, "hps_merge")
+
+
+def hps_leaf_resolve(plan, coef, ub, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, out=None, stream=None):
+    """Leaf solve by re-forming and re-factoring A_ii: u at every node of
+    every leaf from the edge values ub; returns dict(u, info)."""
+    import torch
+    lay = plan.layout
+    if m is None:
+        m = int(ub.numel() // int(lay.o_nb[-1]))
+    _check_dev(coef, "coef", int(6 * lay.o_p2[-1]))
+    _check_dev(ub, "ub", int(lay.o_nb[-1] * m))
+    _check_dev(f, "f", int(lay.o_p2[-1] * m) if f is not None else None)
+    o = dict(out or {})
+    if "u" not in o:
+        o["u"] = torch.empty(int(lay.o_p2[-1] * m), dtype=torch.float64, device=coef.device)
+    if "info" not in o:
+        o["info"] = torch.empty(lay.n_leaves, dtype=torch.int32, device=coef.device)
+    _check_dev(o["u"], "u", int(lay.o_p2[-1] * m))
+    prec_id = PREC[prec] if isinstance(prec, str) else int(prec)
+    status = load_library().hps_leaf_resolve(
+        plan.handle, prec_id, _ptr(coef), _ptr(f), int(m), _ptr(ub), float(tol), int(kmax), _ptr(o["u"]),
+        _ptr(o["info"]), _stream(stream))
+    plan.check(status, "hps_leaf_resolve")
+    return o
+
+
+def hps_leaf_recover(plan, S, W, ub, m, out=None, stream=None):
+    """Leaf solve from stored operators: u_i = S u_b + W per leaf."""
+    import torch
+    lay = plan.layout
+    _check_dev(S, "S", int(lay.o_sb[-1]))
+    _check_dev(ub, "ub", int(lay.o_nb[-1] * m))
+    u = out if out is not None else torch.empty(int(lay.o_p2[-1] * m), dtype=torch.float64, device=S.device)
+    status = load_library().hps_leaf_recover(plan.handle, _ptr(S), _ptr(W), int(m), _ptr(ub), _ptr(u),
+                                             _stream(stream))
+    plan.check(status, "hps_leaf_recover")
+    return u
 
 
 def hps_solve(plan, g, S, W, m, out=None, stream=None):

@@ -169,6 +169,47 @@ def test_condense_manufactured(p, kappa):
     assert e_flux < tol, (e_flux, cond)
 
 
+@pytest.mark.parametrize("p,kappa,m", [(6, 3.0, 1), (12, 30.0, 2), (20, 200.0 / 8, 3)])
+def test_leaf_resolve_manufactured(p, kappa, m):
+    """Section 2 Remark: re-forming the leaf system and solving with the
+    edge values reproduces a degree p-1 tensor polynomial at every non-corner
+    node, for any coefficient samples; corners are returned as 0."""
+    rng = np.random.default_rng(300 + p)
+    box = (0.25, 0.5, 0.0625, 0.125)
+    polys = [random_poly(rng, p - 1, p - 1, xc=0.28125, yc=0.5625, sx=0.03125, sy=0.0625) for _ in range(m)]
+    coef = random_coef(rng, p * p)
+    x, y = O.leaf_nodes(p, box)
+    ix = O.leaf_index_sets(p)
+    uv = np.stack([u(x, y) for u in polys], axis=1)
+    f = np.stack([u.apply_operator(x, y, coef, kappa) for u in polys], axis=1)
+    got = O.leaf_resolve(p, box, coef, kappa, uv[ix["B"]], f)
+    A, _, _, _ = O.leaf_operator(p, box, coef, kappa)
+    cond = np.linalg.cond(A[np.ix_(ix["I"], ix["I"])])
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    assert O.relerr(got[mask], uv[mask]) < max(1e-12, 100 * cond * EPS)
+    assert np.all(got[~mask] == 0.0)
+
+
+def test_leaf_resolve_equals_stored_operators():
+    """The two routes to the interior values agree: a dense solve with the
+    combined right-hand side f_I - A_ib u_b, and the stored S, W of the
+    condensation (u_i = S u_b + W)."""
+    rng = np.random.default_rng(7)
+    p, kappa, m = 14, 40.0, 3
+    box = (0.0, 0.0, 0.125, 0.125)
+    coef = random_coef(rng, p * p)
+    f = rng.standard_normal((p * p, m))
+    ix = O.leaf_index_sets(p)
+    ub = rng.standard_normal((len(ix["B"]), m))
+    out = O.condense_leaf(p, box, coef, kappa, f)
+    ui = O.leaf_interior_solve(out["S"], out["W"], ub)
+    got = O.leaf_resolve(p, box, coef, kappa, ub, f)
+    cond = np.linalg.cond(out["A_ii"])
+    assert O.relerr(got[ix["I"]], ui) < max(1e-12, 100 * cond * EPS)
+    assert np.array_equal(got[ix["B"]], ub)
+
+
 def test_hps_merge_solve_manufactured():
     assert manufactured_grid_error() < 1e-10
 
