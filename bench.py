@@ -528,6 +528,54 @@ def run_gpu(args, rank, ws):
     return line
 
 
+def run_leaf_solve(args, rank, ws):
+    """The two leaf solves after the reduced solve, on the same edge values:
+    u_i = S u_b + W from stored solution operators, against re-forming and
+    re-factoring every leaf (the paper's choice, which keeps no S); plus the
+    condensation with and without storing S, the cost the stored solve
+    carries.  One JSON line."""
+    import torch
+    from paper_2211_14969_b300 import hps
+    w = make_workload(args.workload)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    lay = plan.layout
+    coef_h, f1_h = make_inputs(w, plan)
+    coef = torch.from_numpy(coef_h).cuda()
+    stream = torch.cuda.current_stream()
+    sizes_u = [int(p) ** 2 for p in lay.p]
+    s_bytes = int(lay.o_sb[-1]) * 8
+    res = {}
+    for m in (1, 64):
+        rng = np.random.default_rng(100 + m)
+        f = torch.from_numpy(f1_h if m == w.m else rng.standard_normal(int(lay.o_p2[-1] * m))).cuda()
+        ub = torch.from_numpy(rng.standard_normal(int(lay.o_nb[-1] * m))).cuda()
+        cond = plan.condense(coef, f, m=m, prec="fp64")
+        u_rec = torch.empty(int(lay.o_p2[-1] * m), dtype=torch.float64, device="cuda")
+        t_rec = time_steps(lambda: plan.leaf_recover(cond["S"], cond["W"], ub, m, out=u_rec),
+                           args.steps, args.warmup, ws, stream)
+        row = {"stored_S": {"value": w.n_leaves * args.steps / (t_rec / 1e3), "ms_per_step": t_rec / args.steps}}
+        for prec, name in (("fp64", "refactor_fp64"), ("fp32", "refactor_mixed")):
+            o = {"u": torch.empty_like(u_rec), "info": torch.empty(lay.n_leaves, dtype=torch.int32, device="cuda")}
+            t = time_steps(lambda: plan.leaf_resolve(coef, ub, f, m=m, prec=prec, tol=1e-12, kmax=6, out=o),
+                           args.steps, args.warmup, ws, stream)
+            err = rel_leafwise(o["u"], u_rec, [s * m for s in sizes_u])
+            row[name] = {"value": w.n_leaves * args.steps / (t / 1e3), "ms_per_step": t / args.steps,
+                         "max_leaf_relerr_vs_stored_S": err, "info_nonzero": int((o["info"] != 0).sum()),
+                         "fp64_fallback_leaves": plan.fallback_count() if prec == "fp32" else 0}
+        for prec in ("fp64", "fp32"):
+            for store in (True, False):
+                t = time_steps(lambda: plan.condense(coef, f, m=m, prec=prec, tol=1e-12, kmax=6, store_S=store),
+                               args.steps, args.warmup, ws, stream)
+                row[f"condense_{prec}_{'with' if store else 'without'}_S_ms"] = t / args.steps
+        res[f"m={m}"] = row
+    if rank == 0:
+        print(json.dumps({"metric": "leaf solves/s after the reduced solve: stored S vs re-formed and re-factored leaves",
+                          "unit": "leaf solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "data": "synthetic (random edge values and, for m = 64, loads)",
+                          "config": config_block(args.workload, w, ws), "S_bytes_stored": s_bytes,
+                          "results": res}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,9 +591,13 @@ def main(argv=None):
     ap.add_argument("--workload", default="bumps_p20", choices=sorted(WORKLOADS),
                     help="bumps_p20 (default, the headline workload) or another seeded workload")
     ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the launch")
+    ap.add_argument("--leaf-solve", action="store_true",
+                    help="time the leaf solve after the reduced solve: stored S vs re-factored leaves")
     args = ap.parse_args(argv)
     rank, ws = dist_setup()
-    if args.impl == "reference":
+    if args.leaf_solve:
+        run_leaf_solve(args, rank, ws)
+    elif args.impl == "reference":
         run_reference(args, rank, ws)
     else:
         run_gpu(args, rank, ws)
