@@ -778,12 +778,11 @@ __global__ void __launch_bounds__(NT) dense_solve_kernel(double *base, long long
 __global__ void __launch_bounds__(NT) leaf_recover_all_kernel(LeafTables lt, int m, const double *__restrict__ S,
                                                              const double *__restrict__ W,
                                                              const double *__restrict__ ub, double *__restrict__ u) {
-    const int leaf = blockIdx.x, p = lt.p[leaf], q = p - 2, n = q * q, nbd = 4 * q;
+    const int leaf = blockIdx.x, p = lt.p[leaf], q = p - 2, nbd = 4 * q;
     const double *Sl = S + lt.o_sb[leaf];
     const double *Wl = W ? W + lt.o_ni[leaf] * m : nullptr;
     const double *ul = ub + lt.o_nb[leaf] * m;
     double *uo = u + lt.o_p2[leaf] * m;
-    (void)n;
     for (int e = threadIdx.x; e < p * p * m; e += NT) {
         const int node = e / m, c = e - node * m, i = node / p, j = node - i * p;
         const bool bi = (i == 0 || i == p - 1), bj = (j == 0 || j == p - 1);
