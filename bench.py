@@ -37,17 +37,18 @@ UNIT = "leaf condensations/s"
 
 # DRAM bytes per full 4096-leaf launch from the ncu capture summarised in
 # profiles/condense_kernel_bumps_p20.md (592-leaf case scaled by 4096/592),
-# keyed by the hash of the kernel sources it was taken on; reported only
-# while the sources still hash to that value.
-TRAFFIC_BY_SOURCE = {"d31496ee4646fd38": {"fp32": 30.18e9, "fp64": 72.95e9}}
+# keyed by the hash of the condensation kernel's sources it was taken on;
+# reported only while those sources still hash to that value.
+TRAFFIC_BY_SOURCE = {}
+CONDENSE_SOURCES = ("condense.cu", "dense_lu.cuh", "tc_gemm.cuh", "hps_internal.cuh")
 
 
 def source_hash():
-    import glob
+    """sha256 (first 16 hex digits) of the condensation kernel's sources, in
+    a fixed order."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2211_14969_b300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cu"))) + sorted(glob.glob(os.path.join(csrc, "*.cuh")))
-    files.append(os.path.join(ROOT, "include", "hps.h"))
+    files = [os.path.join(csrc, f) for f in CONDENSE_SOURCES]
     h = hashlib.sha256()
     for f in files:
         with open(f, "rb") as fh:
@@ -576,6 +577,108 @@ def run_leaf_solve(args, rank, ws):
                           "results": res}), flush=True)
 
 
+def merge_flops(q, nx, ny, m):
+    """Algorithmic flops of hps_merge over an nx x ny grid (q edge nodes per
+    leaf side): per merge the LU of Z (2/3 n3^3), the solve for the parent's
+    n_p + m right-hand columns (2 n3^2 (n_p + m)) and, below the root, the
+    parent's [T | h] update (2 n_p n3 (n_p + m)); merges alternate x then y."""
+    wx = wy = 1
+    total = 0.0
+    levels = []
+    while wx < nx or wy < ny:
+        along_x = wx < nx and (wx <= wy or wy == ny)
+        n3 = (wy if along_x else wx) * q
+        npar = 2 * ((2 * wx + wy) if along_x else (wx + 2 * wy)) * q
+        if along_x:
+            wx *= 2
+        else:
+            wy *= 2
+        nm = (nx // wx) * (ny // wy)
+        root = wx == nx and wy == ny
+        f = nm * (2.0 / 3.0 * n3 ** 3 + 2.0 * n3 ** 2 * (npar + m) + (0.0 if root else 2.0 * npar * n3 * (npar + m)))
+        levels.append({"merges": nm, "n3": n3, "n_parent": npar, "gflop": f / 1e9})
+        total += f
+    return total, levels
+
+
+def flux_mismatch(w, lay, out, u, m):
+    """Flux continuity of a solved grid: per leaf the outward flux T u_b + h
+    at its edge nodes [W, E, S, N]; across every interior edge the two
+    leaves' fluxes must cancel.  Returns max |sum| / max |flux|."""
+    import torch
+    p = int(lay.p[0])
+    q, nl = p - 2, lay.n_leaves
+    j = torch.arange(1, p - 1, device=u.device)
+    edge = torch.cat([j, (p - 1) * p + j, j * p, j * p + p - 1])
+    U = u.view(nl, p * p, m)[:, edge, :]
+    flux = torch.bmm(out["T"].view(nl, 4 * q, 4 * q), U) + out["h"].view(nl, 4 * q, m)
+    F = flux.view(w.nx, w.ny, 4, q, m)
+    ew = F[:-1, :, 1] + F[1:, :, 0]          # E of (ix, iy) against W of (ix + 1, iy)
+    sn = F[:, :-1, 3] + F[:, 1:, 2]          # N of (ix, iy) against S of (ix, iy + 1)
+    worst = max(float(ew.abs().max()) if ew.numel() else 0.0, float(sn.abs().max()) if sn.numel() else 0.0)
+    return worst / float(flux.abs().max())
+
+
+def run_merge_solve(args, rank, ws):
+    """The reduced solve after condensation on the same grid: hps_merge
+    (all levels of Schur complements) and hps_solve (downward pass and leaf
+    recovery), with the large levels near the root solved over many CTAs
+    against one CTA per merge on every level.  One JSON line."""
+    import torch
+    from paper_2211_14969_b300 import hps
+    w = make_workload(args.workload)
+    if len(set(int(p) for p in w.p)) != 1:
+        raise SystemExit("--merge-solve needs a uniform-order workload")
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    lay = plan.layout
+    coef_h, f_h = make_inputs(w, plan)
+    coef, f = torch.from_numpy(coef_h).cuda(), torch.from_numpy(f_h).cuda()
+    stream = torch.cuda.current_stream()
+    m = w.m
+    out = plan.condense(coef, f, m=m, prec="fp64")
+    q = int(lay.p[0]) - 2
+    n_outer = 2 * (w.nx + w.ny) * q
+    g = torch.from_numpy(np.random.default_rng(7).standard_normal(n_outer * m)).cuda()
+    flops, levels = merge_flops(q, w.nx, w.ny, m)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    res = {}
+    u_ref = None
+    for name, below, steps, warmup in (("split", -1, args.steps, args.warmup),
+                                       ("one_cta_per_merge", 0, max(1, min(args.steps, 2)), 1)):
+        plan.set_merge_split(below)
+        with ClockSampler(uuid) as ck:
+            t_merge = time_steps(lambda: plan.merge(w.nx, w.ny, out["T"], out["h"], m), steps, warmup, ws, stream)
+        launches = plan.last_launch_count()
+        u = torch.empty(int(lay.o_p2[-1]) * m, dtype=torch.float64, device="cuda")
+        t_solve = time_steps(lambda: plan.solve(g, out["S"], out["W"], m, out=u), steps, warmup, ws, stream)
+        row = {"merge_ms": t_merge / steps, "solve_ms": t_solve / steps,
+               "merge_tflops": flops / (t_merge / steps / 1e3) / 1e12, "merge_launches": launches,
+               "flux_mismatch": flux_mismatch(w, lay, out, u, m), "clocks": ck.summary()}
+        if u_ref is None:
+            u_ref = u.clone()
+        else:
+            row["u_relerr_vs_split"] = float((u - u_ref).norm() / u_ref.norm())
+        res[name] = row
+    if rank == 0:
+        pk = 1.25
+        sp = res["split"]
+        print(json.dumps({"metric": "reduced solve after condensation: hps_merge + hps_solve time",
+                          "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": False, "dtype": "f64",
+                          "data": "synthetic (the workload's FP64 leaf maps; random Dirichlet data)",
+                          "config": config_block(args.workload, w, ws),
+                          "value": sp["merge_ms"] + sp["solve_ms"],
+                          "merge_gflop": flops / 1e9,
+                          "roofline": {"bound": "alu", "achieved": sp["merge_tflops"], "peak": pk, "unit": "TFLOP/s",
+                                       "frac": sp["merge_tflops"] / pk, "traffic": None,
+                                       "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
+                          "levels": levels, "results": res}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -591,12 +694,16 @@ def main(argv=None):
     ap.add_argument("--workload", default="bumps_p20", choices=sorted(WORKLOADS),
                     help="bumps_p20 (default, the headline workload) or another seeded workload")
     ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the launch")
+    ap.add_argument("--merge-solve", action="store_true",
+                    help="time hps_merge + hps_solve on the workload's grid (split vs one CTA per merge)")
     ap.add_argument("--leaf-solve", action="store_true",
                     help="time the leaf solve after the reduced solve: stored S vs re-factored leaves")
     args = ap.parse_args(argv)
     rank, ws = dist_setup()
     if args.leaf_solve:
         run_leaf_solve(args, rank, ws)
+    elif args.merge_solve:
+        run_merge_solve(args, rank, ws)
     elif args.impl == "reference":
         run_reference(args, rank, ws)
     else:

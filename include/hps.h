@@ -140,6 +140,16 @@ hps_status hps_condense(hps_plan *plan, hps_prec prec, const double *d_coef, con
 hps_status hps_merge(hps_plan *plan, int nx, int ny, const double *d_T, const double *d_h, int m,
                      hps_stream stream);
 
+/* How hps_merge solves Z [S3 | w3] = -[Ta31 Tb32 | ha3 + hb3] (the merge
+ * of Section 2 above) on each level.  A level with fewer than `below`
+ * merges runs a blocked LU with partial pivoting whose every step is spread
+ * over many CTAs (the few large merges near the root); the others run one
+ * CTA per merge.  below = -1 (default): the device's SM count; 0: one CTA
+ * per merge everywhere.  Levels whose shared edge exceeds 1599 nodes always
+ * run one CTA per merge.  Both give the same result up to rounding.
+ * Takes effect at the next hps_merge.  HPS_ERR_ARG for below < -1. */
+hps_status hps_set_merge_split(hps_plan *plan, int below);
+
 /* Top-down solve after hps_merge (Section 2 Remark: leaf values from the
  * reduced solution).  d_g: Dirichlet data at the outer edge nodes in the
  * root box order [W, E, S, N] (n_outer x m).  Shared-edge values come from

@@ -40,7 +40,7 @@ struct DevBuf {
 
 struct Level {
     MergeLevelDev dev{};
-    DevBuf maps, aug, th, u, info;
+    DevBuf maps, aug, th, u, info, piv, u3;
 };
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
@@ -104,6 +104,7 @@ struct hps_plan {
     DevBuf u_leaf;
     int merge_nx = 0, merge_ny = 0, merge_m = -1;
     bool merged = false;
+    int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
     std::string err;
 
     hps_status fail(hps_status s, const std::string &msg) {
@@ -537,9 +538,11 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
     cudaStream_t s = (cudaStream_t)stream;
     for (auto &L : P->levels) {
         L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
+        L.piv.release(); L.u3.release();
     }
     P->levels.clear();
     P->merged = false;
+    const int split_below = P->split_below < 0 ? P->sms : P->split_below;
     int wx = 1, wy = 1;
     std::vector<HostLevel> hl;
     while (wx < nx || wy < ny) {
@@ -565,6 +568,9 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         if (!root && (e = L.th.ensure((size_t)H.nm * H.np * (H.np + m) * sizeof(double))) != cudaSuccess) break;
         if ((e = L.u.ensure((size_t)H.nm * H.np * std::max(m, 1) * sizeof(double))) != cudaSuccess) break;
         if ((e = L.info.ensure((size_t)H.nm * sizeof(int))) != cudaSuccess) break;
+        if ((e = L.u3.ensure((size_t)H.nm * H.n3 * std::max(m, 1) * sizeof(double))) != cudaSuccess) break;
+        const bool split = H.nm < split_below && split_solve_fits(H.n3);
+        if (split && (e = L.piv.ensure((size_t)H.nm * H.n3 * sizeof(int))) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(L.maps.p, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         const int *mp = (const int *)L.maps.p;
@@ -578,6 +584,8 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         D.aug = (double *)L.aug.p;
         D.Th = root ? nullptr : (double *)L.th.p;
         D.info = (int *)L.info.p;
+        D.ipiv = split ? (int *)L.piv.p : nullptr;
+        D.u3 = (double *)L.u3.p;
         if ((e = launch_merge_level(D, !root, s)) != cudaSuccess) break;
     }
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_merge");
@@ -588,7 +596,16 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
     P->merge_m = m;
     P->merged = true;
     P->launches = 0;
-    for (auto &L : P->levels) P->launches += (L.dev.Th ? 3 : 2);
+    for (auto &L : P->levels) {
+        const int steps = (L.dev.n3 + 15) / 16;
+        P->launches += 1 + (L.dev.Th ? 1 : 0) + (L.dev.ipiv ? 5 * steps - 2 : 1);
+    }
+    return HPS_OK;
+}
+
+hps_status hps_set_merge_split(hps_plan *P, int below) {
+    if (P == nullptr || below < -1) return HPS_ERR_ARG;
+    P->split_below = below;
     return HPS_OK;
 }
 
@@ -617,7 +634,7 @@ hps_status hps_solve(hps_plan *P, const double *d_g, const double *d_S, const do
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_solve: downward pass");
     e = launch_leaf_recover(P->n_leaves, p, m, d_S, d_W, ub, d_u, s);
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_solve: leaf recovery");
-    P->launches = nl + 1;
+    P->launches = 2 * nl + 1;
     return HPS_OK;
 }
 
@@ -626,6 +643,7 @@ void hps_destroy(hps_plan *P) {
     cudaDeviceSynchronize();
     for (auto &L : P->levels) {
         L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
+        L.piv.release(); L.u3.release();
     }
     P->u_leaf.release();
     P->work.release();

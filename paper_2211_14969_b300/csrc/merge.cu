@@ -8,7 +8,8 @@
 // with every index expressed in the parent's boundary order through per-level
 // maps built on the host.  Downward: u3 = S3 u_parent + w3, children's
 // boundary values gathered from the parent's values and u3, and finally
-// u_i = S u_b + W on every leaf.
+// u_i = S u_b + W on every leaf.  Levels with few merges solve Z over many
+// CTAs (merge_split.cu) instead of one CTA per merge.
 #include <cuda_runtime.h>
 
 #include "hps_internal.cuh"
@@ -132,29 +133,48 @@ __global__ void __launch_bounds__(NT) merge_parent(MergeLevelDev L) {
     }
 }
 
-// u3 = S3 u_parent + w3, then the children's boundary values.
-__global__ void merge_down(MergeLevelDev L, const double *__restrict__ upar, double *__restrict__ uchild) {
-    const int s = blockIdx.x;
-    extern __shared__ double u3[];  // n3 * m
-    const double *aug = L.aug + (long long)s * L.n3 * L.lda;
+// u3 = S3 u_parent + w3: a warp per shared-edge row k, lanes along the
+// parent's boundary, four right-hand columns at a time.
+__global__ void __launch_bounds__(NT) merge_down_u3(MergeLevelDev L, const double *__restrict__ upar) {
+    const int s = blockIdx.y;
+    const int k = blockIdx.x * (NT / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (k >= L.n3) return;
+    const double *row = L.aug + ((long long)s * L.n3 + k) * L.lda + L.c3;
     const double *up = upar + (long long)s * L.np * L.m;
-    for (int e = threadIdx.x; e < L.n3 * L.m; e += NT) {
-        const int k = e / L.m, c = e % L.m;
-        const double *row = aug + (long long)k * L.lda + L.c3;
-        double acc = row[L.np + c];
-        for (int P = 0; P < L.np; ++P) acc = fma(row[P], up[(long long)P * L.m + c], acc);
-        u3[e] = acc;
-    }
-    __syncthreads();
-    for (int chi = 0; chi < 2; ++chi) {
-        const int child = chi == 0 ? L.ca[s] : L.cb[s];
-        const int *src = chi == 0 ? L.srca : L.srcb;
-        double *uc = uchild + (long long)child * L.nbc * L.m;
-        for (int e = threadIdx.x; e < L.nbc * L.m; e += NT) {
-            const int i = e / L.m, c = e % L.m;
-            const int sidx = src[i];
-            uc[e] = sidx >= 0 ? up[(long long)sidx * L.m + c] : u3[(-sidx - 1) * L.m + c];
+    double *out = L.u3 + ((long long)s * L.n3 + k) * L.m;
+    for (int c0 = 0; c0 < L.m; c0 += 4) {
+        const int nc = L.m - c0 < 4 ? L.m - c0 : 4;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int P = lane; P < L.np; P += 32) {
+            const double a = row[P];
+            const double *u = up + (long long)P * L.m + c0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < nc) acc[c] = fma(a, u[c], acc[c]);
         }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+        }
+        if (lane == 0)
+            for (int c = 0; c < nc; ++c) out[c0 + c] = acc[c] + row[L.np + c0 + c];
+    }
+}
+
+// The children's boundary values from the parent's values and u3.
+__global__ void __launch_bounds__(NT) merge_down_scatter(MergeLevelDev L, const double *__restrict__ upar,
+                                                         double *__restrict__ uchild) {
+    const int s = blockIdx.y;
+    const double *up = upar + (long long)s * L.np * L.m;
+    const double *u3 = L.u3 + (long long)s * L.n3 * L.m;
+    const long long per = (long long)L.nbc * L.m;
+    for (long long e = blockIdx.x * (long long)NT + threadIdx.x; e < 2 * per; e += (long long)gridDim.x * NT) {
+        const int chi = (int)(e / per);
+        const int r = (int)(e % per), i = r / L.m, c = r % L.m;
+        const int child = chi == 0 ? L.ca[s] : L.cb[s];
+        const int sidx = (chi == 0 ? L.srca : L.srcb)[i];
+        uchild[(long long)child * per + r] = sidx >= 0 ? up[(long long)sidx * L.m + c] : u3[(-sidx - 1) * L.m + c];
     }
 }
 
@@ -197,7 +217,10 @@ cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStr
     merge_build_aug<<<dim3(gx, L.nm), NT, 0, s>>>(L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_dense_solve(L.aug, (long long)L.n3 * L.lda, L.n3, L.c3, C, L.lda, L.nm, L.info, s);
+    if (L.ipiv)
+        e = launch_split_solve(L, L.ipiv, s);
+    else
+        e = launch_dense_solve(L.aug, (long long)L.n3 * L.lda, L.n3, L.c3, C, L.lda, L.nm, L.info, s);
     if (e != cudaSuccess) return e;
     if (form_parent) {
         const int ldt = L.np + L.m;
@@ -209,12 +232,13 @@ cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStr
 }
 
 cudaError_t launch_merge_down(const MergeLevelDev &L, const double *upar, double *uchild, cudaStream_t s) {
-    const size_t smem = (size_t)L.n3 * L.m * sizeof(double);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(merge_down, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    merge_down<<<L.nm, NT, smem, s>>>(L, upar, uchild);
+    merge_down_u3<<<dim3((L.n3 + NT / 32 - 1) / (NT / 32), L.nm), NT, 0, s>>>(L, upar);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long work = 2LL * L.nbc * L.m;
+    int gx = (int)((work + NT - 1) / NT);
+    if (gx > 64) gx = 64;
+    merge_down_scatter<<<dim3(gx, L.nm), NT, 0, s>>>(L, upar, uchild);
     return cudaGetLastError();
 }
 

@@ -24,9 +24,17 @@ struct MergeLevelDev {
     double *aug;                     // [nm][n3][lda]: [Z | 0 | S3 | w3] after the solve
     double *Th;                      // [nm][np][np + m]: parent [T | h]
     int *info;                       // [nm] zero-pivot step of Z (0 = none)
+    int *ipiv;                       // [nm][n3] pivot rows: Z solved over many CTAs; null: one CTA per merge
+    double *u3;                      // [nm][n3][m] shared-edge values of the downward pass
 };
 
 cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s);
+// [Z | 0 | B] -> [U | 0 | X] for every merge of a level, one blocked-LU step
+// per launch with each step spread over many CTAs (merge_split.cu).  Needs
+// L.ipiv; cudaErrorInvalidValue when the panel of n3 rows does not fit
+// shared memory (split_solve_fits).
+cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s);
+bool split_solve_fits(int n3);
 cudaError_t launch_merge_down(const MergeLevelDev &L, const double *upar, double *uchild, cudaStream_t s);
 cudaError_t launch_leaf_recover(int n_leaves, int p, int m, const double *S, const double *W,
                                 const double *ub, double *u, cudaStream_t s);

@@ -1,0 +1,284 @@
+// Dense solves of the upper merge levels spread over many CTAs.
+//
+// A merge solves Z X = B with Z = Ta33 + Tb33 (n3 x n3) and
+// B = -[Ta31 Tb32 | ha3 + hb3]; the HPS merge of two boxes (Section 2 of
+// arXiv 2211.14969 takes it from its references).  Near the root of a
+// uniform tree there are few merges and each is large (a 64 x 64 grid of
+// p = 20 leaves ends with one merge of n3 = 1152 and 4609 right-hand
+// columns), so one CTA per merge would leave all but a handful of SMs
+// idle.  Here every level with few merges runs a right-looking blocked LU
+// with partial pivoting on the augmented row-major matrix
+// [Z | 0 | B] -> [U | 0 | X], one launch per step, with the work of each
+// step spread over column blocks and 64 x 64 output tiles:
+//
+//   for each panel of NB columns at k:
+//     panel:      factor rows k.. of columns k..k+NB-1 (one CTA per merge,
+//                 panel in shared memory, block-wide argmax per column);
+//     swap_lower: apply the panel's interchanges to the columns right of the
+//                 panel and solve the unit-lower L11 for the NB rows at k
+//                 (one thread per column);
+//     gemm:       A22 -= L21 U12 over 64 x 64 tiles;
+//   then for each block row kb from the bottom:
+//     upper:      X1 = U11^{-1} Y1 on the NB rows at kb (thread per column);
+//     gemm:       Y0 -= U01 X1 on the rows above.
+//
+// The multipliers of L are not applied to earlier columns: the right-hand
+// side is eliminated together with Z, so L is never needed again and the
+// columns left of a panel keep its multipliers in their unswapped rows.
+// info[s] receives the first step with an exactly zero pivot (1-based),
+// as LAPACK's getrf does; the elimination then continues without scaling.
+#include <cuda_runtime.h>
+
+#include "merge.cuh"
+
+namespace hps {
+namespace {
+
+constexpr int PNT = 256;   // threads of the panel kernel
+constexpr int CNT = 128;   // threads (columns) of the triangular kernels
+constexpr int GT = 64;     // gemm output tile (GT x GT), 256 threads, 4 x 4 each
+
+// Panel factorization.  P (column-major, ld = odd >= rows) holds rows
+// k..n3-1 of columns k..k+nbk-1.
+template <int NB>
+__global__ void __launch_bounds__(PNT) split_panel(double *__restrict__ aug, long long stride, int n3, int lda,
+                                                   int k, int nbk, int *__restrict__ ipiv, int *__restrict__ info) {
+    extern __shared__ double P[];
+    __shared__ double wv[PNT / 32];
+    __shared__ int wi[PNT / 32];
+    __shared__ int pivs;
+    const int s = blockIdx.x;
+    double *A = aug + (long long)s * stride;
+    const int rows = n3 - k;
+    const int ld = rows | 1;
+    for (int e = threadIdx.x; e < rows * NB; e += PNT) {
+        const int r = e / NB, c = e % NB;
+        P[c * ld + r] = c < nbk ? A[(long long)(k + r) * lda + k + c] : 0.0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j < nbk; ++j) {
+        // argmax |P[j.., j]|, ties to the smallest row
+        double best = -1.0;
+        int bi = rows;
+        for (int r = j + threadIdx.x; r < rows; r += PNT) {
+            const double v = fabs(P[j * ld + r]);
+            if (v > best) { best = v; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { wv[warp] = best; wi[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = wv[0];
+            int i = wi[0];
+            for (int w = 1; w < PNT / 32; ++w)
+                if (wv[w] > b || (wv[w] == b && wi[w] < i)) { b = wv[w]; i = wi[w]; }
+            if (!(b > 0.0)) {
+                i = j;  // exact zero column: no interchange, no scaling
+                if (info[s] == 0) info[s] = k + j + 1;
+            }
+            pivs = i;
+            ipiv[(long long)s * n3 + k + j] = k + i;
+        }
+        __syncthreads();
+        const int pr = pivs;
+        if (pr != j) {
+            for (int c = threadIdx.x; c < nbk; c += PNT) {
+                const double t = P[c * ld + j];
+                P[c * ld + j] = P[c * ld + pr];
+                P[c * ld + pr] = t;
+            }
+            __syncthreads();
+        }
+        const double d = P[j * ld + j];
+        if (d != 0.0) {
+            const double rd = 1.0 / d;
+            for (int r = j + 1 + threadIdx.x; r < rows; r += PNT) {
+                const double l = P[j * ld + r] * rd;
+                P[j * ld + r] = l;
+                for (int c = j + 1; c < nbk; ++c) P[c * ld + r] = fma(-l, P[c * ld + j], P[c * ld + r]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < rows * nbk; e += PNT) {
+        const int r = e / nbk, c = e % nbk;
+        A[(long long)(k + r) * lda + k + c] = P[c * ld + r];
+    }
+}
+
+// Interchanges and the unit-lower solve for the columns right of the panel.
+template <int NB>
+__global__ void __launch_bounds__(CNT) split_swap_lower(double *__restrict__ aug, long long stride, int n3, int lda,
+                                                        int k, int nbk, int C, const int *__restrict__ ipiv) {
+    __shared__ double L[NB][NB];
+    __shared__ int pv[NB];
+    const int s = blockIdx.y;
+    double *A = aug + (long long)s * stride;
+    for (int e = threadIdx.x; e < NB * NB; e += CNT) {
+        const int i = e / NB, j = e % NB;
+        L[i][j] = (i < nbk && j < nbk) ? A[(long long)(k + i) * lda + k + j] : 0.0;
+    }
+    if (threadIdx.x < NB) pv[threadIdx.x] = threadIdx.x < nbk ? ipiv[(long long)s * n3 + k + threadIdx.x] : 0;
+    __syncthreads();
+    const int col = k + nbk + blockIdx.x * CNT + threadIdx.x;
+    if (col >= C) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < nbk) {
+            const int r = pv[j];
+            double *a = A + (long long)(k + j) * lda + col;
+            if (r != k + j) {
+                double *b = A + (long long)r * lda + col;
+                const double t = *a;
+                *a = *b;
+                *b = t;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < nbk) {
+            double v = A[(long long)(k + j) * lda + col];
+#pragma unroll
+            for (int i = 0; i < j; ++i) v = fma(-L[j][i], x[i], v);
+            x[j] = v;
+        } else {
+            x[j] = 0.0;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < nbk) A[(long long)(k + j) * lda + col] = x[j];
+}
+
+// X1 = U11^{-1} Y1 for the right-hand columns of block row kb.
+template <int NB>
+__global__ void __launch_bounds__(CNT) split_upper(double *__restrict__ aug, long long stride, int lda, int kb, int nbk,
+                                                   int c0, int C) {
+    __shared__ double U[NB][NB];
+    const int s = blockIdx.y;
+    double *A = aug + (long long)s * stride;
+    for (int e = threadIdx.x; e < NB * NB; e += CNT) {
+        const int i = e / NB, j = e % NB;
+        U[i][j] = (i < nbk && j < nbk) ? A[(long long)(kb + i) * lda + kb + j] : 1.0;
+    }
+    __syncthreads();
+    const int col = c0 + blockIdx.x * CNT + threadIdx.x;
+    if (col >= C) return;
+    double x[NB];
+#pragma unroll
+    for (int j = NB - 1; j >= 0; --j) {
+        if (j < nbk) {
+            double v = A[(long long)(kb + j) * lda + col];
+#pragma unroll
+            for (int i = j + 1; i < NB; ++i)
+                if (i < nbk) v = fma(-U[j][i], x[i], v);
+            x[j] = v / U[j][j];
+        } else {
+            x[j] = 0.0;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (j < nbk) A[(long long)(kb + j) * lda + col] = x[j];
+}
+
+// C[r0 + i][c0 + j] -= sum_t A[r0 + i][ka + t] * A[kb + t][c0 + j], t < K <= KM,
+// over GT x GT tiles of the nr x nc block (all inside one merge's matrix).
+template <int KM>
+__global__ void __launch_bounds__(256) split_gemm(double *__restrict__ aug, long long stride, int lda, int r0, int nr,
+                                                  int c0, int nc, int ka, int kb, int K) {
+    __shared__ double As[KM][GT + 1];
+    __shared__ double Bs[KM][GT];
+    const int s = blockIdx.z;
+    double *A = aug + (long long)s * stride;
+    const int tr = blockIdx.y * GT, tc = blockIdx.x * GT;
+    for (int e = threadIdx.x; e < GT * KM; e += 256) {
+        const int i = e / KM, t = e % KM;
+        As[t][i] = (tr + i < nr && t < K) ? A[(long long)(r0 + tr + i) * lda + ka + t] : 0.0;
+    }
+    for (int e = threadIdx.x; e < KM * GT; e += 256) {
+        const int t = e / GT, j = e % GT;
+        Bs[t][j] = (t < K && tc + j < nc) ? A[(long long)(kb + t) * lda + c0 + tc + j] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // outputs (ty + 16u, tx + 16v)
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+#pragma unroll
+    for (int t = 0; t < KM; ++t) {
+        double a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = As[t][ty + 16 * u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) b[v] = Bs[t][tx + 16 * v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = tr + ty + 16 * u;
+        if (i >= nr) continue;
+        double *row = A + (long long)(r0 + i) * lda + c0 + tc;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = tx + 16 * v;
+            if (tc + j < nc) row[j] -= acc[u][v];
+        }
+    }
+}
+
+}  // namespace
+
+constexpr int kSplitNB = 16;
+
+bool split_solve_fits(int n3) { return (size_t)((n3 | 1) * kSplitNB) * sizeof(double) <= 200 * 1024; }
+
+cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t st) {
+    constexpr int NB = kSplitNB;
+    const int n3 = L.n3, lda = L.lda, nm = L.nm;
+    const int C = L.c3 + L.np + L.m;
+    const long long stride = (long long)n3 * lda;
+    if (ipiv == nullptr || !split_solve_fits(n3)) return cudaErrorInvalidValue;
+    const size_t psmem = (size_t)((n3 | 1) * NB) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(split_panel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(L.info, 0, (size_t)nm * sizeof(int), st)) != cudaSuccess) return e;
+    for (int k = 0; k < n3; k += NB) {
+        const int nbk = n3 - k < NB ? n3 - k : NB;
+        const size_t sm = (size_t)(((n3 - k) | 1) * NB) * sizeof(double);
+        split_panel<NB><<<nm, PNT, sm, st>>>(L.aug, stride, n3, lda, k, nbk, ipiv, L.info);
+        const int cr = C - (k + nbk);
+        if (cr > 0) split_swap_lower<NB><<<dim3((cr + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, k, nbk, C, ipiv);
+        const int nr = n3 - (k + nbk);
+        if (nr > 0 && cr > 0)
+            split_gemm<NB><<<dim3((cr + GT - 1) / GT, (nr + GT - 1) / GT, nm), 256, 0, st>>>(
+                L.aug, stride, lda, k + nbk, nr, k + nbk, cr, k, k, nbk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int nrhs = C - L.c3;
+    const int last = ((n3 - 1) / NB) * NB;
+    for (int kb = last; kb >= 0; kb -= NB) {
+        const int nbk = n3 - kb < NB ? n3 - kb : NB;
+        split_upper<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, lda, kb, nbk, L.c3, C);
+        if (kb > 0)
+            split_gemm<NB><<<dim3((nrhs + GT - 1) / GT, (kb + GT - 1) / GT, nm), 256, 0, st>>>(
+                L.aug, stride, lda, 0, kb, L.c3, nrhs, kb, kb, nbk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace hps

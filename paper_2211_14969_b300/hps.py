@@ -58,6 +58,7 @@ def load_library():
     L.hps_set_timing.argtypes = [vp, i]
     L.hps_set_blocking.argtypes = [vp, i, i]
     L.hps_set_fp64_fallback.argtypes = [vp, i]
+    L.hps_set_merge_split.argtypes = [vp, i]
     L.hps_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.hps_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     L.hps_last_launch_count.argtypes = [vp]
@@ -67,7 +68,8 @@ def load_library():
     L.hps_destroy.restype = None
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_merge", "hps_solve",
-                 "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_fallback_count",
+                 "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split",
+                 "hps_fallback_count",
                  "hps_phase_times", "hps_last_launch_count"):
         getattr(L, name).restype = i
     _lib = L
@@ -169,6 +171,10 @@ class Plan:
     def set_fp64_fallback(self, on=True):
         """Mixed path: re-condense non-converged leaves in FP64 (default on)."""
         self.check(load_library().hps_set_fp64_fallback(self.handle, int(bool(on))), "hps_set_fp64_fallback")
+
+    def set_merge_split(self, below=-1):
+        """Levels with fewer than `below` merges solve over many CTAs (-1: SM count; 0: never)."""
+        self.check(load_library().hps_set_merge_split(self.handle, int(below)), "hps_set_merge_split")
 
     def fallback_count(self):
         n = ctypes.c_int()

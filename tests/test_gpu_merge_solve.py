@@ -15,9 +15,11 @@ from paper_2211_14969_b300 import workloads as WL
 pytestmark = pytest.mark.gpu
 
 
-def gpu_pipeline(w, prec="fp64", coef_fn=None, load_fn=None, g_fn=None):
+def gpu_pipeline(w, prec="fp64", coef_fn=None, load_fn=None, g_fn=None, split=None):
     p = int(w.p[0])
     plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    if split is not None:
+        plan.set_merge_split(split)
     coef, f, _ = gpu_inputs(w, plan, coef_fn, load_fn)
     out = plan.condense(coef, f, m=1, prec=prec, tol=1e-13, kmax=8)
     plan.merge(w.nx, w.ny, out["T"], out["h"], 1)
@@ -151,3 +153,73 @@ def test_larger_and_rectangular_grids_match_oracle(nx, ny, p):
     mask = np.ones(p * p, bool)
     mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
     assert rel(u_gpu[:, mask], u_ora[:, mask]) < 1e-11
+
+
+EVERY_LEVEL_SPLIT = 1 << 30
+
+
+@pytest.mark.parametrize("nx,ny,p", [(8, 8, 9), (8, 8, 13), (4, 16, 12)])
+def test_split_and_one_cta_merges_match_oracle(nx, ny, p):
+    """The merge solve over many CTAs on every level, and one CTA per merge
+    on every level, both against the oracle's merge tree.  Shared edges of
+    56 (p = 9) and 88 (p = 13) nodes end in a ragged 8-row panel; 4 x 16
+    merges x once, then y alone."""
+    w = WL.bumps(p=p, nx=nx, ny=ny, kappa=25.0, seed=7, m=1)
+    w.dirichlet = "planewave"
+    sol, _, _ = oracle_pipeline(w)
+    u_ora = grid_from_sol(sol, p)
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    for split in (0, EVERY_LEVEL_SPLIT):
+        u_gpu = gpu_pipeline(w, split=split)
+        assert rel(u_gpu[:, mask], u_ora[:, mask]) < 1e-12, split
+
+
+def test_merge_split_argument_error():
+    w = WL.planewave(p=6, nx=2, ny=2)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    with pytest.raises(hps.HpsError):
+        plan.set_merge_split(-2)
+
+
+def test_full_size_grid_reproduces_manufactured_polynomial():
+    """The benchmark's grid: 64 x 64 leaves of p = 20 (12 merge levels, a
+    root interface of 1152 nodes), kappa = 200 with the bumps_p20 field b.
+    A tensor polynomial of degree 19 in x and y is the exact discrete
+    solution on every leaf, so condense + merge + solve must reproduce it
+    to rounding at every node; the default schedule (the levels near the
+    root solved over many CTAs) and one CTA per merge must agree."""
+    p, n = 20, 64
+    w = WL.bumps_p20()
+    rng = np.random.default_rng(2020)
+    u = random_poly(rng, p - 1, p - 1, xc=0.5, yc=0.5, sx=0.5, sy=0.5)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    xy = plan.leaf_nodes().cpu().numpy().reshape(n * n, 2, p * p)
+    x, y = xy[:, 0], xy[:, 1]
+    coef = np.moveaxis(w.coefficients(x, y), 0, 1)                 # (leaves, 6, p^2)
+    f = u.apply_operator(x, y, np.moveaxis(coef, 1, 0), w.kappa)   # (leaves, p^2)
+    exact = u(x, y)
+    out = plan.condense(torch.from_numpy(coef.ravel()).cuda(), torch.from_numpy(f.ravel()).cuda(),
+                        m=1, prec="fp64")
+    q = p - 2
+    j = np.arange(1, p - 1)
+    ix = np.arange(n)
+    # outer edge nodes, root order [W, E, S, N], each side by increasing coordinate
+    W = exact[ix][:, j].ravel()
+    E = exact[(n - 1) * n + ix][:, (p - 1) * p + j].ravel()
+    S = exact[ix * n][:, j * p].ravel()
+    N = exact[ix * n + n - 1][:, j * p + p - 1].ravel()
+    g = torch.from_numpy(np.concatenate([W, E, S, N])).cuda()
+    assert g.numel() == 4 * n * q
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    sols = []
+    for split in (-1, 0):
+        plan.set_merge_split(split)
+        plan.merge(n, n, out["T"], out["h"], 1)
+        sols.append(plan.solve(g, out["S"], out["W"], 1).cpu().numpy().reshape(n * n, p * p))
+    torch.cuda.synchronize()
+    assert (out["info"].cpu().numpy() == 0).all()
+    for us in sols:
+        assert rel(us[:, mask], exact[:, mask]) < 1e-9
+    assert rel(sols[0][:, mask], sols[1][:, mask]) < 1e-10
