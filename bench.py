@@ -39,7 +39,7 @@ UNIT = "leaf condensations/s"
 # profiles/condense_kernel_bumps_p20.md (592-leaf case scaled by 4096/592),
 # keyed by the hash of the condensation kernel's sources it was taken on;
 # reported only while those sources still hash to that value.
-TRAFFIC_BY_SOURCE = {}
+TRAFFIC_BY_SOURCE = {"13575c81aaa347eb": {"fp32": 30.51e9, "fp64": 73.02e9}}
 CONDENSE_SOURCES = ("condense.cu", "dense_lu.cuh", "tc_gemm.cuh", "hps_internal.cuh")
 
 
@@ -492,6 +492,30 @@ def run_gpu(args, rank, ws):
         for sp, *_ in subs:
             sp.close()
 
+    # the reduced solve on the same grid, from the FP64 leaf maps: every
+    # merge level (hps_merge) and the downward pass with leaf recovery
+    # (hps_solve) for random Dirichlet data
+    reduced = None
+    if (len(set(int(v) for v in w.p)) == 1 and not args.leaves and "fp64" in outs
+            and w.nx * w.ny == n and (w.nx & (w.nx - 1)) == 0 and (w.ny & (w.ny - 1)) == 0):
+        o = outs["fp64"]
+        q = int(w.p[0]) - 2
+        g = torch.from_numpy(np.random.default_rng(7).standard_normal(2 * (w.nx + w.ny) * q * m)).cuda()
+        u = torch.empty(int(lay.o_p2[-1]) * m, dtype=torch.float64, device="cuda")
+        rs = max(2, args.steps // 3)
+        with ClockSampler(uuid) as cs:
+            t_merge = time_steps(lambda: plan.merge(w.nx, w.ny, o["T"], o["h"], m), rs, 1, ws, stream)
+        merge_launches = plan.last_launch_count()
+        t_solve = time_steps(lambda: plan.solve(g, o["S"], o["W"], m, out=u), rs, 1, ws, stream)
+        mflops, _ = merge_flops(q, w.nx, w.ny, m)
+        tf = mflops / (t_merge / rs * 1e-3) / 1e12
+        reduced = {"merge_ms": t_merge / rs, "solve_ms": t_solve / rs, "merge_gflop": mflops / 1e9,
+                   "merge_tflops": tf,
+                   "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s", "frac": tf / 1.25,
+                                "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
+                   "gpu_launches_merge": merge_launches, "flux_mismatch": flux_mismatch(w, lay, o, u, m),
+                   "clocks": cs.summary()}
+
     line = None
     if rank == 0:
         cpu = None
@@ -522,6 +546,8 @@ def run_gpu(args, rank, ws):
                 "mixed_leaves_recondensed_in_fp64": r32["fp64_fallback_leaves"],
                 "cpu_baseline": cpu,
                 "parity_vs_oracle_sampled": parity}
+        if reduced is not None:
+            line["reduced_solve_fp64"] = reduced
         if per_order is not None:
             line["per_order_launches"] = per_order
         print(json.dumps(line), flush=True)

@@ -122,8 +122,12 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
  *            FP64 info code; hps_set_fp64_fallback(plan, 0) turns that off,
  *            and such a leaf then reports info = -kmax with the last
  *            iterate.  Ignored for HPS_FP64.
- * Corner rows: with c12 != 0 the interior rows touch the leaf corners, whose
- * columns are dropped (corners are not unknowns). */
+ * Corners: with c12 != 0 the interior rows touch the leaf corners, which are
+ * not unknowns; a corner's value is taken as the mean of the polynomial
+ * extrapolations (degree p-3) along its two edges from their p-2 edge
+ * nodes, so its column is folded into the edge columns (A_ib + A_ic E).
+ * Exact for tensor polynomials of degree <= p-3; with c12 == 0 no row
+ * touches a corner. */
 hps_status hps_condense(hps_plan *plan, hps_prec prec, const double *d_coef, const double *d_f,
                         int m, double tol, int kmax, double *d_S, double *d_T, double *d_h,
                         double *d_W, int *d_info, hps_stream stream);

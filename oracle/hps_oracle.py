@@ -35,9 +35,12 @@ boxes as a Schur complement on their shared edge.
 Readings where the paper is silent (each is also listed in the design notes):
 * p is the number of Chebyshev points per direction (degree p-1).
 * Leaf corners are not unknowns.  With c12 == 0 no interior or normal row
-  touches a corner, so dropping them is exact; rows of a c12 != 0 operator
-  that touch a corner are not condensed here (parity unpinned for c12 != 0
-  condensation; assembly with c12 != 0 is pinned).
+  touches a corner, so dropping them is exact.  With c12 != 0 the mixed
+  derivative at an interior node reaches the four corners; each corner
+  value is then taken as the average of the two polynomial extrapolations,
+  of degree p-3, through the p-2 edge nodes of its two adjacent edges
+  (corner_extrapolation), so the corner columns fold into the edge columns:
+  A_ib <- A_ib + A_ic E.  Exact for tensor polynomials of degree <= p-3.
 * Node id i*p + j, i the x index; interior nodes lexicographic (i major);
   boundary order [W, E, S, N], each edge by increasing coordinate.
 * Normal rows use the outward normal: -d/dx on W, +d/dx on E, -d/dy on S,
@@ -109,6 +112,50 @@ def leaf_index_sets(p):
     return {"I": I, "W": W, "E": E, "S": S, "N": N, "B": W + E + S + N}
 
 
+def corner_extrapolation(p):
+    """E (4 x n_b): the corner values from the edge values.
+
+    Corners in node order [(0, 0), (0, p-1), (p-1, 0), (p-1, p-1)] (node id
+    i*p + j, i the x index); edge nodes in the boundary order [W, E, S, N].
+    A corner's value is the mean of the extrapolations along its two
+    adjacent edges, each the polynomial of degree p-3 through that edge's
+    p-2 interior Chebyshev nodes evaluated at the edge's end (the reading
+    for c12 != 0, where the mixed derivative reaches the corners).  Lagrange
+    basis by its product formula.
+    """
+    q = p - 2
+    t = cheb_points(p)[1:p - 1]          # interior nodes on [-1, 1], increasing
+
+    def ends(at):
+        out = np.ones(q)
+        for k in range(q):
+            for m in range(q):
+                if m != k:
+                    out[k] *= (at - t[m]) / (t[k] - t[m])
+        return out
+
+    lo, hi = ends(-1.0), ends(1.0)
+    W, E, S, N = (slice(0, q), slice(q, 2 * q), slice(2 * q, 3 * q), slice(3 * q, 4 * q))
+    Emat = np.zeros((4, 4 * q))
+    # (x, y) = (-1, -1): along W to y = -1, along S to x = -1
+    Emat[0, W] += 0.5 * lo
+    Emat[0, S] += 0.5 * lo
+    # (-1, +1): W to y = +1, N to x = -1
+    Emat[1, W] += 0.5 * hi
+    Emat[1, N] += 0.5 * lo
+    # (+1, -1): E to y = -1, S to x = +1
+    Emat[2, E] += 0.5 * lo
+    Emat[2, S] += 0.5 * hi
+    # (+1, +1): E to y = +1, N to x = +1
+    Emat[3, E] += 0.5 * hi
+    Emat[3, N] += 0.5 * hi
+    return Emat
+
+
+def corner_ids(p):
+    return [0, p - 1, (p - 1) * p, p * p - 1]
+
+
 def leaf_operator(p, box, coef, kappa):
     """Full p^2 x p^2 collocation matrix of the leaf and its normal rows.
 
@@ -161,7 +208,7 @@ def condense_leaf(p, box, coef, kappa, f=None):
     ix = leaf_index_sets(p)
     I, B = ix["I"], ix["B"]
     A_ii = A[np.ix_(I, I)]
-    A_ib = A[np.ix_(I, B)]
+    A_ib = interior_edge_block(A, p)
     N_b = Nrow[:, B]
     N_i = Nrow[:, I]
     lu = sla.lu_factor(A_ii)
@@ -174,6 +221,18 @@ def condense_leaf(p, box, coef, kappa, f=None):
         out["W"] = W
         out["h"] = N_i @ W
     return out
+
+
+def interior_edge_block(A, p):
+    """A_ib with the corner columns folded in through the corner
+    extrapolation: A_ib + A_ic E (A_ic is zero when c12 == 0)."""
+    ix = leaf_index_sets(p)
+    I, B = ix["I"], ix["B"]
+    A_ib = A[np.ix_(I, B)]
+    A_ic = A[np.ix_(I, corner_ids(p))]
+    if np.any(A_ic != 0.0):
+        A_ib = A_ib + A_ic @ corner_extrapolation(p)
+    return A_ib
 
 
 def leaf_interior_solve(S, W, u_b):
@@ -196,7 +255,7 @@ def leaf_resolve(p, box, coef, kappa, u_b, f=None):
     ix = leaf_index_sets(p)
     I, B = ix["I"], ix["B"]
     u_b = np.asarray(u_b, dtype=np.float64).reshape(len(B), -1)
-    rhs = -A[np.ix_(I, B)] @ u_b
+    rhs = -interior_edge_block(A, p) @ u_b
     if f is not None:
         rhs = rhs + np.asarray(f, dtype=np.float64).reshape(p * p, -1)[I]
     u = np.zeros((p * p, u_b.shape[1]))

@@ -114,7 +114,11 @@ __device__ __forceinline__ int edge_index(int k, int l, int p, int q) {
 // M (row-major, ld LDC) <- [A_ii | 0 | -A_ib | f_I] for the operator
 //   -(c11 u_xx + 2 c12 u_xy + c22 u_yy + c1 u_x + c2 u_y) - kappa^2 b u,
 // one warp per row.  The row is zeroed, then only the nodes that share a
-// grid line with the row's node are written (all nodes when c12 != 0).  The
+// grid line with the row's node are written (all nodes when c12 != 0).
+// Corners are not unknowns: with c12 != 0 the mixed term reaches them, and a
+// corner's value is the mean of the degree p-3 extrapolations along its two
+// edges, so its entry is added to the edge columns with the weights
+// l_l(-1)/2, l_l(+1)/2 that follow D*D in the tables.  The
 // entries are formed in the working precision from per-row factors and the
 // differentiation matrices held in that precision.  In FP32 the per-row
 // factors are the coefficients (truncated to float on their bit patterns)
@@ -174,12 +178,21 @@ __device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restri
             if (k == i && l == j) v -= dg;
             return v;
         };
+        const T *cw = D2w + p2;   // corner weights: [0, p) to the low end, [p, 2p) to the high end
         auto put = [&](int k, int l) {
             const bool bk = (k == 0 || k == p - 1), bl = (l == 0 || l == p - 1);
             if (bk && bl) return;  // corners are not unknowns
-            const T v = entry(k, l);
-            if (!bk && !bl) row[(k - 1) * q + (l - 1)] = v;
-            else row[L.n4 + edge_index(k, l, p, q)] = -v;
+            T v = entry(k, l);
+            if (!bk && !bl) {
+                row[(k - 1) * q + (l - 1)] = v;
+                return;
+            }
+            if (dense) {
+                // the two corners at the ends of this node's edge
+                if (bk) v += cw[l] * entry(k, 0) + cw[p + l] * entry(k, p - 1);
+                else v += cw[k] * entry(0, l) + cw[p + k] * entry(p - 1, l);
+            }
+            row[L.n4 + edge_index(k, l, p, q)] = -v;
         };
         if (!dense) {
             for (int t = lane; t < 2 * p; t += 32) {
@@ -416,7 +429,26 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                                 const int e = ((k - 1) * q + (l - 1)) * cwp + cc;
                                 return make_float2(Xh[e], Xl[e]);
                             }
-                            if ((k == 0 || k == p - 1) && (l == 0 || l == p - 1)) return make_float2(0.0f, 0.0f);
+                            if ((k == 0 || k == p - 1) && (l == 0 || l == p - 1)) {
+                                // the mean of the extrapolations along the corner's two edges
+                                const int o = 2 * p2;
+                                const int wl = (l == 0 ? 0 : p), wk = (k == 0 ? 0 : p);
+                                const int ev = (k == 0 ? 0 : q), eh = (l == 0 ? 2 * q : 3 * q);   // its W/E and S/N edge
+                                if constexpr (RESOLVE) {
+                                    DF acc = {0.0f, 0.0f};
+                                    for (int t2 = 1; t2 <= q; ++t2) {
+                                        const DF a = df_from(ub[(long long)(ev + t2 - 1) * L.m + c]);
+                                        const DF b = df_from(ub[(long long)(eh + t2 - 1) * L.m + c]);
+                                        df_mac(acc, Dh[o + wl + t2], Dl[o + wl + t2], a.hi, a.lo);
+                                        df_mac(acc, Dh[o + wk + t2], Dl[o + wk + t2], b.hi, b.lo);
+                                    }
+                                    acc = df_norm(acc);
+                                    return make_float2(acc.hi, acc.lo);
+                                }
+                                if (c >= ev && c < ev + q) return make_float2(Dh[o + wl + c - ev + 1], Dl[o + wl + c - ev + 1]);
+                                if (c >= eh && c < eh + q) return make_float2(Dh[o + wk + c - eh + 1], Dl[o + wk + c - eh + 1]);
+                                return make_float2(0.0f, 0.0f);
+                            }
                             if constexpr (RESOLVE) {
                                 const DF e = df_from(ub[(long long)edge_index(k, l, p, q) * L.m + c]);
                                 return make_float2(e.hi, e.lo);

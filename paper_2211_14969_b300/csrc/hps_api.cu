@@ -71,6 +71,31 @@ void chebyshev_matrix(int p, std::vector<double> &D) {
     }
 }
 
+// Corner extrapolation weights of order p: the Lagrange basis of the p - 2
+// interior Chebyshev points t_1..t_q of [-1, 1] evaluated at the ends,
+// halved (a corner is the mean of the extrapolations along its two edges):
+// ce[l] = l_l(-1) / 2 and ce[p + l] = l_l(+1) / 2 for l = 1..q, zero at
+// l = 0 and p - 1.  Barycentric form with w_k = 1 / prod_{m != k}(t_k - t_m).
+void corner_weights(int p, std::vector<double> &ce) {
+    const int q = p - 2, N = p - 1;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> t(q), w(q);
+    for (int k = 0; k < q; ++k) t[k] = -std::cos(pi * (k + 1) / N);
+    for (int k = 0; k < q; ++k) {
+        double d = 1.0;
+        for (int m = 0; m < q; ++m)
+            if (m != k) d *= (t[k] - t[m]);
+        w[k] = 1.0 / d;
+    }
+    ce.assign(2 * (size_t)p, 0.0);
+    for (int side = 0; side < 2; ++side) {
+        const double s = side ? 1.0 : -1.0;
+        double den = 0.0;
+        for (int k = 0; k < q; ++k) den += w[k] / (s - t[k]);
+        for (int k = 0; k < q; ++k) ce[(size_t)side * p + k + 1] = 0.5 * (w[k] / (s - t[k])) / den;
+    }
+}
+
 }  // namespace
 
 namespace hps {
@@ -211,6 +236,9 @@ hps_status hps_build_leaves(const hps_leaf_desc *desc, hps_plan **out, hps_strea
                 for (int k = 0; k < p; ++k) s += D[(size_t)i * p + k] * D[(size_t)k * p + j];
                 dmat.push_back(s);
             }
+        std::vector<double> ce;
+        corner_weights(p, ce);
+        dmat.insert(dmat.end(), ce.begin(), ce.end());
     }
     cudaError_t err = cudaGetDevice(&P->device);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, P->device);

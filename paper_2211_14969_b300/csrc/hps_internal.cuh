@@ -23,7 +23,9 @@ struct LeafTables {
 };
 
 // Chebyshev differentiation matrices on [-1, 1] for every order in the plan:
-// D of order p at dmat + doff[p], followed by D*D.
+// D of order p at dmat + doff[p], followed by D*D and the 2p corner
+// extrapolation weights (l_l(-1)/2 then l_l(+1)/2 for the Lagrange basis of
+// the interior nodes l = 1..p-2, zero at l = 0 and p-1).
 struct DTables {
     const double *dmat;
     const float *dmat32;  // the same tables rounded to FP32, same offsets

@@ -59,7 +59,8 @@ cudaError_t scratch_address(int dev, void **out) {
 
 // Per-call set-up in the scratch: uniform-p leaf tables (order p, packed
 // offsets, identity work order), the Chebyshev matrix D of order p on
-// [-1, 1] and D*D, and a zeroed work counter.  D follows the same definition
+// [-1, 1], D*D and the corner extrapolation weights, and a zeroed work
+// counter.  D follows the same definition
 // as the plan path (barycentric weights, product form of the node
 // differences, diagonal from the zero row sum).
 __global__ void noalloc_setup(int n_leaves, int p, int *pv, long long *off, int *order, int *doff,
@@ -101,6 +102,28 @@ __global__ void noalloc_setup(int n_leaves, int p, int *pv, long long *off, int 
         for (int k = 0; k < p; ++k) s += D[i * p + k] * D[k * p + j];
         D2[e] = s;
     }
+    // corner extrapolation weights, as the plan path: the Lagrange basis of
+    // the interior nodes t_1..t_q at -1 and +1, halved (barycentric form)
+    double *ce = D2 + p * p;
+    for (int e = threadIdx.x; e < 2 * p; e += blockDim.x) {
+        const int side = e / p, l = e % p;
+        double v = 0.0;
+        if (l >= 1 && l <= q) {
+            const double s = side ? 1.0 : -1.0;
+            double den = 0.0, num = 0.0;
+            for (int k = 1; k <= q; ++k) {
+                const double tk = -cospi((double)k / N);
+                double w = 1.0;
+                for (int mm = 1; mm <= q; ++mm)
+                    if (mm != k) w *= (tk + cospi((double)mm / N));
+                const double term = (1.0 / w) / (s - tk);
+                den += term;
+                if (k == l) num = term;
+            }
+            v = 0.5 * num / den;
+        }
+        ce[e] = v;
+    }
 }
 
 hps_status fail(hps_status s, const std::string &msg) {
@@ -125,7 +148,7 @@ extern "C" hps_status hps_condense_noalloc(int n_leaves, int p, double kappa, co
     const size_t o_ord = align256(o_off + 5 * nl * sizeof(long long));
     const size_t o_doff = align256(o_ord + nl * sizeof(int));
     const size_t o_dmat = align256(o_doff + (HPS_PMAX + 1) * sizeof(int));
-    const size_t o_queue = align256(o_dmat + 2 * (size_t)p * p * sizeof(double));
+    const size_t o_queue = align256(o_dmat + (2 * (size_t)p * p + 2 * (size_t)p) * sizeof(double));
     const size_t o_work = align256(o_queue + sizeof(int));
     const long long q = p - 2, n = q * q, r = 4 * q + m, C = ((n + 3) & ~3LL) + r, LDC = (C + 3) & ~3LL;
     const size_t slot = align256((size_t)(n * LDC) * sizeof(double));

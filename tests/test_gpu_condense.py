@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle.hps_oracle as O
-from gpu_cases import assert_within, compare_leaves, gpu_inputs
+from gpu_cases import assert_within, compare_leaves, gpu_inputs, leaf_slices, relerr
 from paper_2211_14969_b300 import hps
 from paper_2211_14969_b300 import workloads as WL
 
@@ -116,14 +116,51 @@ def test_annulus_variable_coefficients(prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_mixed_derivative_term(prec):
-    """c12 != 0 (the mixed-derivative term of Eq. (chain_rule)); corner
-    columns are dropped on both sides."""
+    """c12 != 0 (the mixed-derivative term of Eq. (chain_rule)); the
+    corners enter on both sides through the corner extrapolation."""
     def coef_fn(x, y):
         one = np.ones_like(x)
         return np.stack([1.0 + 0.2 * x, 0.15 * np.sin(3 * y), 1.0 + 0.1 * y, 0.3 * one, -0.2 * x,
                          1.0 - 0.3 * np.cos(2 * x)])
     w = WL.bumps(p=14, nx=16, ny=16, kappa=40.0, seed=3, m=1)
     check(Sub(w, [0, 77, 255]), prec, coef_fn=coef_fn)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mixed_term_reproduces_degree_p_minus_3_polynomial(prec):
+    """c12 != 0 with random coefficient samples on every leaf: a tensor
+    polynomial of degree p-3 (exact under the corner extrapolation) gives
+    S u_b + W = u_i and T u_b + h = its analytic outward normal derivative."""
+    from manufactured import random_coef, random_poly
+    p = 12
+    w = WL.bumps(p=p, nx=4, ny=4, kappa=20.0, seed=5, m=1)
+    sub = Sub(w, list(range(16)))
+    rng = np.random.default_rng(123)
+    u = random_poly(rng, p - 3, p - 3, xc=0.5, yc=0.5, sx=0.5, sy=0.5)
+    cache = {}
+
+    def coef_fn(x, y):
+        key = (round(float(np.min(x)), 12), round(float(np.min(y)), 12))
+        if key not in cache:
+            cache[key] = random_coef(np.random.default_rng(abs(hash(key)) % (2 ** 32)), x.size, c12=True)
+        return cache[key]
+
+    def load_fn(x, y):
+        return u.apply_operator(x, y, coef_fn(x, y), w.kappa)[:, None]
+
+    plan, out = run(sub, prec, tol=1e-13, coef_fn=coef_fn, load_fn=load_fn)
+    assert (out["info"].cpu().numpy() == 0).all()
+    cpu = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    ix = O.leaf_index_sets(p)
+    for l in range(16):
+        x, y = O.leaf_nodes(p, sub.box[l])
+        got = leaf_slices(plan.layout, cpu, l, 1)
+        uv = u(x, y)[:, None]
+        dudx, dudy = u(x, y, 1, 0), u(x, y, 0, 1)
+        dn = np.concatenate([-dudx[ix["W"]], dudx[ix["E"]], -dudy[ix["S"]], dudy[ix["N"]]])[:, None]
+        e_int = relerr(got["S"] @ uv[ix["B"]] + got["W"], uv[ix["I"]])
+        e_flux = relerr(got["T"] @ uv[ix["B"]] + got["h"], dn)
+        assert e_int < 1e-10 and e_flux < 1e-10, (l, e_int, e_flux)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])

@@ -169,6 +169,68 @@ def test_condense_manufactured(p, kappa):
     assert e_flux < tol, (e_flux, cond)
 
 
+@pytest.mark.parametrize("p", [4, 5, 10, 20, 42])
+def test_corner_extrapolation_exact_to_degree_p_minus_3(p):
+    """Each corner from its two edges: exact for tensor polynomials of degree
+    <= p-3 in each variable (the interpolant through p-2 points), each row a
+    pair of partitions of unity, and not exact at degree p-2."""
+    rng = np.random.default_rng(40 + p)
+    box = (0.25, 0.5, 0.125, 0.0625)
+    x, y = O.leaf_nodes(p, box)
+    ix = O.leaf_index_sets(p)
+    E = O.corner_extrapolation(p)
+    corners = [0, p - 1, (p - 1) * p, p * p - 1]
+    assert np.allclose(E.sum(axis=1), 1.0, rtol=0, atol=1e-12)
+    u = random_poly(rng, p - 3, p - 3, xc=0.3125, yc=0.53125, sx=0.0625, sy=0.03125)
+    got, ref = E @ u(x, y)[ix["B"]], u(x, y)[corners]
+    assert O.relerr(got, ref) < 1e-11, O.relerr(got, ref)
+    # eta^(p-2): along W and E the extrapolation misses by the node
+    # polynomial omega(t) = prod (t - t_k) over the p-2 interior Chebyshev
+    # points t_k = -cos(k pi / (p-1)); along S and N it is constant (exact)
+    C = np.zeros((1, p - 1))
+    C[0, p - 2] = 1.0
+    v = TensorPoly(C, xc=0.3125, yc=0.53125, sx=0.0625, sy=0.03125)
+    tk = -np.cos(np.arange(1, p - 1) * np.pi / (p - 1))
+    om = {s: np.prod(s - tk) for s in (-1.0, 1.0)}
+    miss = np.array([om[-1.0], om[1.0], om[-1.0], om[1.0]])   # corners at y = -1, +1, -1, +1
+    got_v = E @ v(x, y)[ix["B"]]
+    assert np.allclose(got_v - v(x, y)[corners], -0.5 * miss, rtol=1e-9, atol=1e-13)
+
+
+@pytest.mark.parametrize("p,kappa", [(6, 3.0), (10, 20.0), (16, 40.0), (24, 50.0)])
+def test_condense_with_mixed_term_manufactured(p, kappa):
+    """c12 != 0: the corners enter through the corner extrapolation, so a
+    tensor polynomial of degree p-3 is reproduced exactly by S u_b + W and
+    T u_b + h (its analytic normal derivative), for any coefficient
+    samples; at degree p-1 it is not (the corner values are extrapolated)."""
+    rng = np.random.default_rng(500 + p)
+    box = (0.5, 0.25, 0.125, 0.0625)
+    coef = random_coef(rng, p * p, c12=True)
+    u = random_poly(rng, p - 3, p - 3, xc=0.5625, yc=0.28125, sx=0.0625, sy=0.03125)
+    e_int, e_flux, cond = condense_errors(p, box, coef, kappa, u)
+    tol = max(1e-12, 100 * cond * EPS)
+    assert e_int < tol, (e_int, cond)
+    assert e_flux < tol, (e_flux, cond)
+    v = random_poly(rng, p - 1, p - 1, xc=0.5625, yc=0.28125, sx=0.0625, sy=0.03125)
+    assert condense_errors(p, box, coef, kappa, v)[0] > 100 * tol
+
+
+def test_leaf_resolve_with_mixed_term_manufactured():
+    """The re-formed leaf solve with c12 != 0 folds the corners the same way:
+    exact for a degree p-3 tensor polynomial."""
+    rng = np.random.default_rng(77)
+    p, kappa = 12, 15.0
+    box = (0.25, 0.5, 0.0625, 0.125)
+    coef = random_coef(rng, p * p, c12=True)
+    u = random_poly(rng, p - 3, p - 3, xc=0.28125, yc=0.5625, sx=0.03125, sy=0.0625)
+    x, y = O.leaf_nodes(p, box)
+    ix = O.leaf_index_sets(p)
+    uv = u(x, y)[:, None]
+    f = u.apply_operator(x, y, coef, kappa)[:, None]
+    got = O.leaf_resolve(p, box, coef, kappa, uv[ix["B"]], f)
+    assert O.relerr(got[ix["I"]], uv[ix["I"]]) < 1e-11
+
+
 @pytest.mark.parametrize("p,kappa,m", [(6, 3.0, 1), (12, 30.0, 2), (20, 200.0 / 8, 3)])
 def test_leaf_resolve_manufactured(p, kappa, m):
     """Section 2 Remark: re-forming the leaf system and solving with the
@@ -316,7 +378,8 @@ def test_pins_pass_unmutated():
 
 
 @pytest.mark.parametrize("mutation", ["transpose_D", "flip_west_normal", "drop_c1",
-                                      "kappa_sign", "c12_factor", "swap_merge_order"])
+                                      "kappa_sign", "c12_factor", "swap_merge_order",
+                                      "corner_ends_swapped", "corners_dropped"])
 def test_planted_mistake_is_caught(monkeypatch, mutation):
     real_diff, real_op, real_keys = O.cheb_diff, O.leaf_operator, O.box_keys
     if mutation == "transpose_D":
@@ -344,6 +407,18 @@ def test_planted_mistake_is_caught(monkeypatch, mutation):
             A, N, Dx, Dy = real_op(p, box, coef, kappa)
             return A + np.asarray(coef[1], float)[:, None] * (Dx @ Dy), N, Dx, Dy
         monkeypatch.setattr(O, "leaf_operator", op)
+    if mutation in ("corner_ends_swapped", "corners_dropped"):
+        real_E = O.corner_extrapolation
+        if mutation == "corner_ends_swapped":
+            monkeypatch.setattr(O, "corner_extrapolation", lambda p: real_E(p)[::-1])
+        else:
+            monkeypatch.setattr(O, "corner_extrapolation", lambda p: 0.0 * real_E(p))
+        rng = np.random.default_rng(9)
+        p, box = 9, (0.0, 0.0, 0.25, 0.125)
+        u = random_poly(rng, p - 3, p - 3, xc=0.125, yc=0.0625, sx=0.125, sy=0.0625)
+        e_int, e_flux, _ = condense_errors(p, box, random_coef(rng, p * p, c12=True), 5.0, u)
+        assert max(e_int, e_flux) > 1e-6, (e_int, e_flux)
+        return
     if mutation == "c12_factor":
         rng = np.random.default_rng(8)
         p, box = 8, (0.0, 0.0, 0.25, 0.125)
