@@ -132,6 +132,33 @@ hps_status hps_condense(hps_plan *plan, hps_prec prec, const double *d_coef, con
                         int m, double tol, int kmax, double *d_S, double *d_T, double *d_h,
                         double *d_W, int *d_info, hps_stream stream);
 
+/* Maximum pipeline depth of hps_condense_host. */
+#define HPS_HOST_MAX_CHUNKS 64
+
+/* hps_condense with every input and output in HOST memory: the same leaf
+ * condensation (Section 2, static condensation of the leaf interiors) and
+ * the same arguments, packing and info codes as hps_condense, with h_*
+ * host pointers in place of d_*.  The leaves are split into `chunks`
+ * contiguous ranges of about equal work (0: 8; at most
+ * HPS_HOST_MAX_CHUNKS and n_leaves); each range's inputs are copied to the
+ * device on one copy stream, condensed by one launch (ranges alternate
+ * between the given stream and a second compute stream, each with half of
+ * a doubled workspace), and its outputs copied back on another copy
+ * stream, so transfers overlap the condensation.  The results are the
+ * ones hps_condense computes (each leaf is condensed by the same code).
+ * Host buffers should be page-locked (cudaHostAlloc / pinned): pageable
+ * memory gives correct results but the copies then do not overlap.
+ * The call returns once everything is enqueued; it completes on `stream`
+ * (synchronize it before reading the host outputs).  The plan keeps device
+ * copies of all inputs and outputs (allocated on first use, about the size
+ * of the caller's arrays), two more streams and their events until
+ * hps_destroy.  Successive calls on one plan must be issued on the same
+ * stream (or be ordered by the caller).  Errors as hps_condense;
+ * HPS_ERR_ARG also for chunks outside 0..HPS_HOST_MAX_CHUNKS. */
+hps_status hps_condense_host(hps_plan *plan, hps_prec prec, const double *h_coef, const double *h_f,
+                             int m, double tol, int kmax, double *h_S, double *h_T, double *h_h,
+                             double *h_W, int *h_info, int chunks, hps_stream stream);
+
 /* Upward merges over a uniform-p nx x ny grid of leaves tiling a rectangle
  * (leaf l = ix*ny + iy), nx and ny powers of two.  Each merge of boxes
  * alpha, beta across their shared edge 3 (1, 2 their other edges) forms

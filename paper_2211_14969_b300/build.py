@@ -60,6 +60,8 @@ def build(force=False, verbose=False):
     common = [*ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
         common.insert(0, "-Xptxas=-v")
+    if os.environ.get("HPS_SPLIT_COMPILE") == "1":   # faster rebuilds while iterating
+        common.append("--split-compile=0")
     os.makedirs(OBJ, exist_ok=True)
     objs, cmds = [], []
     for f in SOURCES:

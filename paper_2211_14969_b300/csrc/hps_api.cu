@@ -130,6 +130,12 @@ struct hps_plan {
     int merge_nx = 0, merge_ny = 0, merge_m = -1;
     bool merged = false;
     int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
+    // hps_condense_host: device copies of the inputs and outputs, the chunk
+    // work-queue orders and counters, two more streams and their events
+    DevBuf hstage, horder;
+    std::vector<int> horder_host;         // kept alive until its upload completes
+    cudaStream_t hs_comp = nullptr, hs_h2d = nullptr, hs_d2h = nullptr;
+    std::vector<cudaEvent_t> hev;
     std::string err;
 
     hps_status fail(hps_status s, const std::string &msg) {
@@ -304,12 +310,24 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
     return HPS_OK;
 }
 
-// The condensation launch, shared by hps_condense and hps_leaf_resolve
-// (d_ub != nullptr: leaf solve, outputs in d_u).  Arguments checked by the
-// callers except the ones both share.
+// One launch over a subset of the leaves (hps_condense_host): its work-queue
+// order, length and counter, and which half of a doubled workspace its CTAs
+// use (so two consecutive subsets can run concurrently).
+struct CondenseChunk {
+    const int *order;
+    int n;
+    int *queue;
+    int half;
+};
+
+// The condensation launch, shared by hps_condense, hps_leaf_resolve
+// (d_ub != nullptr: leaf solve, outputs in d_u) and hps_condense_host (ck:
+// one subset of the leaves; the caller resets the counters).  Arguments
+// checked by the callers except the ones all share.
 static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef, const double *d_f, int m,
                                double tol, int kmax, double *d_S, double *d_T, double *d_h, double *d_W,
-                               int *d_info, const double *d_ub, double *d_u, hps_stream stream) {
+                               int *d_info, const double *d_ub, double *d_u, hps_stream stream,
+                               const CondenseChunk *ck = nullptr) {
     if (prec != HPS_FP64 && (kmax < 0 || !(tol >= 0.0)))
         return P->fail(HPS_ERR_ARG, "hps_condense: kmax < 0 or tol < 0");
     const bool mixed = prec != HPS_FP64;
@@ -329,7 +347,8 @@ static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef,
     }
     const int per_sm = condense_max_ctas_per_sm(prec, blk);
     if (per_sm < 1) return P->fail(forced ? HPS_ERR_ARG : HPS_ERR_CUDA, "hps_condense: kernel does not fit on an SM");
-    const int grid = std::min(P->n_leaves, P->sms * per_sm);
+    const int full_grid = std::min(P->n_leaves, P->sms * per_sm);
+    const int grid = ck ? std::min(ck->n, full_grid) : full_grid;
     long long slot = 0;
     for (int p = P->pmin; p <= P->pmax; ++p) {
         const long long q = p - 2, n = q * q, r = 4 * q + m, C = round_up(n, 4) + r, LDC = round_up(C, 4);
@@ -340,7 +359,7 @@ static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef,
         }
         slot = std::max(slot, round_up(b, 256));
     }
-    cudaError_t e = P->work.ensure((size_t)slot * grid);
+    cudaError_t e = P->work.ensure((size_t)slot * full_grid * (ck ? 2 : 1));
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense: workspace");
     CondenseParams prm{};
     prm.blk = blk;
@@ -359,9 +378,14 @@ static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef,
     prm.h = m > 0 ? d_h : nullptr;
     prm.W = m > 0 ? d_W : nullptr;
     prm.info = d_info;
-    prm.work = (unsigned char *)P->work.p;
+    prm.work = (unsigned char *)P->work.p + (ck ? (size_t)ck->half * slot * full_grid : 0);
     prm.slot_bytes = slot;
     prm.queue = P->d_queue;
+    if (ck) {
+        prm.lt.order = ck->order;
+        prm.n_leaves = ck->n;
+        prm.queue = ck->queue;
+    }
     prm.tol = tol;
     prm.kmax = kmax;
     prm.fallbacks = P->d_queue + 1;
@@ -369,6 +393,11 @@ static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef,
     prm.ub = d_ub;
     prm.u = d_u;
     cudaStream_t s = (cudaStream_t)stream;
+    if (ck) {
+        e = launch_condense(prec, prm, grid, s);
+        if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense_host: launch");
+        return HPS_OK;
+    }
     e = cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(int), s);
     P->last_stream = s;
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense: queue reset");
@@ -400,6 +429,147 @@ hps_status hps_condense(hps_plan *P, hps_prec prec, const double *d_coef, const 
     if (m > 0 && (d_f == nullptr || d_h == nullptr))
         return P->fail(HPS_ERR_ARG, "hps_condense: m > 0 needs d_f and d_h");
     return run_condense(P, prec, d_coef, d_f, m, tol, kmax, d_S, d_T, d_h, d_W, d_info, nullptr, nullptr, stream);
+}
+
+hps_status hps_condense_host(hps_plan *P, hps_prec prec, const double *h_coef, const double *h_f, int m,
+                             double tol, int kmax, double *h_S, double *h_T, double *h_h, double *h_W,
+                             int *h_info, int chunks, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (prec != HPS_FP64 && prec != HPS_MIXED_FP32 && prec != HPS_MIXED_TF32 && prec != HPS_MIXED_BF16)
+        return P->fail(HPS_ERR_ARG, "hps_condense_host: unknown precision");
+    if (h_coef == nullptr || h_T == nullptr || h_info == nullptr)
+        return P->fail(HPS_ERR_ARG, "hps_condense_host: h_coef, h_T and h_info are required");
+    if (m < 0) return P->fail(HPS_ERR_ARG, "hps_condense_host: m < 0");
+    if (m > 0 && (h_f == nullptr || h_h == nullptr))
+        return P->fail(HPS_ERR_ARG, "hps_condense_host: m > 0 needs h_f and h_h");
+    if (chunks < 0 || chunks > HPS_HOST_MAX_CHUNKS)
+        return P->fail(HPS_ERR_ARG, "hps_condense_host: chunks outside 0..HPS_HOST_MAX_CHUNKS");
+    const int nl = P->n_leaves;
+    int nc = chunks == 0 ? 8 : chunks;
+    nc = std::max(1, std::min(nc, nl));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    // streams and events, made once per plan
+    for (cudaStream_t *sp : {&P->hs_comp, &P->hs_h2d, &P->hs_d2h})
+        if (*sp == nullptr && (e = cudaStreamCreateWithFlags(sp, cudaStreamNonBlocking)) != cudaSuccess)
+            return P->cuda_fail(e, "hps_condense_host: stream");
+    const size_t nev = 3 * (size_t)HPS_HOST_MAX_CHUNKS + 1;
+    while (P->hev.size() < nev) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return P->cuda_fail(e, "hps_condense_host: event");
+        P->hev.push_back(ev);
+    }
+    cudaEvent_t ev_start = P->hev[0];
+    auto ev_in = [&](int c) { return P->hev[1 + 3 * c]; };
+    auto ev_out = [&](int c) { return P->hev[2 + 3 * c]; };
+    auto ev_back = [&](int c) { return P->hev[3 + 3 * c]; };
+    // device copies of every input and output, packed as the caller's arrays
+    // offsets of leaf l in each packed array for l = 0..nl (the plan keeps
+    // the exclusive prefix sums of the first nl leaves)
+    auto at = [&](const std::vector<long long> &v, int l, int kind) -> long long {
+        if (l < nl) return v[l];
+        const long long q = P->p[nl - 1] - 2, sz[5] = {(q + 2) * (q + 2), q * q, 4 * q, q * q * 4 * q, 16 * q * q};
+        return v[nl - 1] + sz[kind];
+    };
+    auto o_p2 = [&](int l) { return at(P->o_p2, l, 0); };
+    auto o_ni = [&](int l) { return at(P->o_ni, l, 1); };
+    auto o_nb = [&](int l) { return at(P->o_nb, l, 2); };
+    auto o_sb = [&](int l) { return at(P->o_sb, l, 3); };
+    auto o_bb = [&](int l) { return at(P->o_bb, l, 4); };
+    const long long np2 = o_p2(nl), nni = o_ni(nl), nnb = o_nb(nl), nsb = o_sb(nl), nbb = o_bb(nl);
+    const size_t b_coef = (size_t)6 * np2 * 8, b_f = (size_t)np2 * m * 8, b_S = h_S ? (size_t)nsb * 8 : 0;
+    const size_t b_T = (size_t)nbb * 8, b_h = (size_t)nnb * m * 8, b_W = h_W ? (size_t)nni * m * 8 : 0;
+    const size_t o_f = round_up(b_coef, 256), o_S = o_f + round_up(b_f, 256), o_T = o_S + round_up(b_S, 256);
+    const size_t o_h = o_T + round_up(b_T, 256), o_W = o_h + round_up(b_h, 256), o_i = o_W + round_up(b_W, 256);
+    const size_t o_q = o_i + round_up((size_t)nl * sizeof(int), 256);
+    const size_t total = o_q + (size_t)HPS_HOST_MAX_CHUNKS * sizeof(int);
+    if ((e = P->hstage.ensure(total)) != cudaSuccess) return P->cuda_fail(e, "hps_condense_host: staging buffers");
+    if ((e = P->horder.ensure((size_t)nl * sizeof(int))) != cudaSuccess)
+        return P->cuda_fail(e, "hps_condense_host: chunk orders");
+    unsigned char *base = (unsigned char *)P->hstage.p;
+    double *d_coef = (double *)base, *d_f = m > 0 ? (double *)(base + o_f) : nullptr;
+    double *d_S = h_S ? (double *)(base + o_S) : nullptr, *d_T = (double *)(base + o_T);
+    double *d_h = m > 0 ? (double *)(base + o_h) : nullptr;
+    double *d_W = (h_W && m > 0) ? (double *)(base + o_W) : nullptr;
+    int *d_info = (int *)(base + o_i), *d_q = (int *)(base + o_q);
+    // contiguous leaf ranges of about equal work (n_i^3), each queued
+    // largest leaves first
+    std::vector<int> cut(nc + 1, nl);
+    {
+        std::vector<double> acc(nl + 1, 0.0);
+        for (int l = 0; l < nl; ++l) {
+            const double ni = (double)(P->p[l] - 2) * (P->p[l] - 2);
+            acc[l + 1] = acc[l] + ni * ni * ni;
+        }
+        cut[0] = 0;
+        int l = 0;
+        for (int c = 1; c < nc; ++c) {
+            const double target = acc[nl] * c / nc;
+            while (l < nl && acc[l + 1] <= target) ++l;
+            cut[c] = std::max(cut[c - 1] + 1, std::min(l, nl - (nc - c)));
+        }
+    }
+    // the previous call's upload of the orders must be done before the host
+    // vector is rewritten
+    if ((e = cudaStreamSynchronize(P->hs_h2d)) != cudaSuccess) return P->cuda_fail(e, "hps_condense_host: sync");
+    P->horder_host.resize(nl);
+    for (int c = 0; c < nc; ++c) {
+        int *o = P->horder_host.data() + cut[c];
+        for (int l = cut[c]; l < cut[c + 1]; ++l) o[l - cut[c]] = l;
+        std::stable_sort(o, o + (cut[c + 1] - cut[c]), [&](int x, int y) { return P->p[x] > P->p[y]; });
+    }
+    // everything earlier on the caller's stream comes first
+    e = cudaMemsetAsync(d_q, 0, (size_t)HPS_HOST_MAX_CHUNKS * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+    for (cudaStream_t t : {P->hs_comp, P->hs_h2d, P->hs_d2h})
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(t, ev_start, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->horder.p, P->horder_host.data(), (size_t)nl * sizeof(int), cudaMemcpyHostToDevice,
+                            P->hs_h2d);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense_host: set-up");
+    P->last_stream = s;
+    auto h2d = [&](void *d, const void *h, size_t off, size_t bytes) {
+        return bytes ? cudaMemcpyAsync((char *)d + off, (const char *)h + off, bytes, cudaMemcpyHostToDevice, P->hs_h2d)
+                     : cudaSuccess;
+    };
+    auto d2h = [&](void *h, const void *d, size_t off, size_t bytes) {
+        return bytes ? cudaMemcpyAsync((char *)h + off, (const char *)d + off, bytes, cudaMemcpyDeviceToHost, P->hs_d2h)
+                     : cudaSuccess;
+    };
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        const int a = cut[c], b = cut[c + 1];
+        e = h2d(d_coef, h_coef, (size_t)6 * o_p2(a) * 8, (size_t)6 * (o_p2(b) - o_p2(a)) * 8);
+        if (e == cudaSuccess && m > 0)
+            e = h2d(d_f, h_f, (size_t)o_p2(a) * m * 8, (size_t)(o_p2(b) - o_p2(a)) * m * 8);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in(c), P->hs_h2d);
+        // chunks alternate between the caller's stream and the second compute
+        // stream, each with its own half of the workspace
+        cudaStream_t cs = (c & 1) ? P->hs_comp : s;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in(c), 0);
+        if (e != cudaSuccess) break;
+        CondenseChunk ck{(const int *)P->horder.p + a, b - a, d_q + c, c & 1};
+        hps_status st = run_condense(P, prec, d_coef, d_f, m, tol, kmax, d_S, d_T, d_h, d_W, d_info, nullptr, nullptr,
+                                     (hps_stream)cs, &ck);
+        if (st != HPS_OK) return st;
+        e = cudaEventRecord(ev_out(c), cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P->hs_d2h, ev_out(c), 0);
+        if (e == cudaSuccess && h_S) e = d2h(h_S, d_S, (size_t)o_sb(a) * 8, (size_t)(o_sb(b) - o_sb(a)) * 8);
+        if (e == cudaSuccess) e = d2h(h_T, d_T, (size_t)o_bb(a) * 8, (size_t)(o_bb(b) - o_bb(a)) * 8);
+        if (e == cudaSuccess && m > 0)
+            e = d2h(h_h, d_h, (size_t)o_nb(a) * m * 8, (size_t)(o_nb(b) - o_nb(a)) * m * 8);
+        if (e == cudaSuccess && h_W && m > 0)
+            e = d2h(h_W, d_W, (size_t)o_ni(a) * m * 8, (size_t)(o_ni(b) - o_ni(a)) * m * 8);
+        if (e == cudaSuccess) e = d2h(h_info, d_info, (size_t)a * sizeof(int), (size_t)(b - a) * sizeof(int));
+        if (e == cudaSuccess) e = cudaEventRecord(ev_back(c), P->hs_d2h);
+    }
+    // the call completes on the caller's stream
+    // (the copy stream waited for every chunk's launch before its copies)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_back(nc - 1), 0);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense_host");
+    P->launches = nc;
+    return HPS_OK;
 }
 
 hps_status hps_leaf_resolve(hps_plan *P, hps_prec prec, const double *d_coef, const double *d_f, int m,
@@ -674,6 +844,11 @@ void hps_destroy(hps_plan *P) {
         L.piv.release(); L.u3.release();
     }
     P->u_leaf.release();
+    P->hstage.release();
+    P->horder.release();
+    for (cudaStream_t t : {P->hs_comp, P->hs_h2d, P->hs_d2h})
+        if (t) cudaStreamDestroy(t);
+    for (cudaEvent_t ev : P->hev) cudaEventDestroy(ev);
     P->work.release();
     P->tables.release();
     for (cudaEvent_t ev : P->ev) cudaEventDestroy(ev);

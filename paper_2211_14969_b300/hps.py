@@ -51,6 +51,7 @@ def load_library():
     L.hps_build_leaves.argtypes = [ctypes.POINTER(_LeafDesc), ctypes.POINTER(vp), vp]
     L.hps_leaf_nodes.argtypes = [vp, vp, vp]
     L.hps_condense.argtypes = [vp, i, vp, vp, i, d, i, vp, vp, vp, vp, vp, vp]
+    L.hps_condense_host.argtypes = [vp, i, vp, vp, i, d, i, vp, vp, vp, vp, vp, i, vp]
     L.hps_merge.argtypes = [vp, i, i, vp, vp, i, vp]
     L.hps_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.hps_leaf_resolve.argtypes = [vp, i, vp, vp, i, vp, d, i, vp, vp, vp]
@@ -67,7 +68,7 @@ def load_library():
     L.hps_destroy.argtypes = [vp]
     L.hps_destroy.restype = None
     L.hps_version.restype = i
-    for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_merge", "hps_solve",
+    for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_condense_host", "hps_merge", "hps_solve",
                  "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split",
                  "hps_fallback_count",
                  "hps_phase_times", "hps_last_launch_count"):
@@ -150,6 +151,10 @@ class Plan:
     def condense(self, coef, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, store_S=True,
                  store_W=True, out=None, stream=None):
         return hps_condense(self, coef, f, m, prec, tol, kmax, store_S, store_W, out, stream)
+
+    def condense_host(self, coef, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, store_S=True,
+                      store_W=True, out=None, chunks=0, stream=None):
+        return hps_condense_host(self, coef, f, m, prec, tol, kmax, store_S, store_W, out, chunks, stream)
 
     def merge(self, nx, ny, T, h, m, stream=None):
         return hps_merge(self, nx, ny, T, h, m, stream)
@@ -253,6 +258,53 @@ def hps_condense(plan, coef, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, sto
         plan.handle, prec_id, _ptr(coef), _ptr(f), int(m), float(tol), int(kmax), _ptr(o.get("S")),
         _ptr(o["T"]), _ptr(o.get("h")), _ptr(o.get("W")), _ptr(o["info"]), _stream(stream))
     plan.check(status, "hps_condense")
+    return o
+
+
+def _check_host(t, name, numel=None):
+    if t is None:
+        return
+    if t.device.type != "cpu" or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous CPU tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+
+
+def hps_condense_host(plan, coef, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, store_S=True,
+                      store_W=True, out=None, chunks=0, stream=None):
+    """hps_condense with host (CPU) tensors in and out; copies and launches
+    overlap in chunks.  Outputs are allocated pinned when not given.  The
+    call is asynchronous on `stream`: synchronize before reading outputs."""
+    import torch
+    lay = plan.layout
+    if m is None:
+        m = 0 if f is None else int(f.numel() // int(lay.o_p2[-1]))
+    _check_host(coef, "coef", int(6 * lay.o_p2[-1]))
+    _check_host(f, "f", int(lay.o_p2[-1] * m) if f is not None else None)
+    o = dict(out or {})
+
+    def empty(n, dt=torch.float64):
+        return torch.empty(int(n), dtype=dt).pin_memory()
+    if "T" not in o:
+        o["T"] = empty(lay.o_bb[-1])
+    if store_S and "S" not in o:
+        o["S"] = empty(lay.o_sb[-1])
+    if m > 0 and "h" not in o:
+        o["h"] = empty(lay.o_nb[-1] * m)
+    if m > 0 and store_W and "W" not in o:
+        o["W"] = empty(lay.o_ni[-1] * m)
+    if "info" not in o:
+        o["info"] = empty(lay.n_leaves, torch.int32)
+    _check_host(o.get("S"), "S", int(lay.o_sb[-1]))
+    _check_host(o["T"], "T", int(lay.o_bb[-1]))
+    _check_host(o.get("h"), "h", int(lay.o_nb[-1] * m) if m > 0 else None)
+    _check_host(o.get("W"), "W", int(lay.o_ni[-1] * m) if m > 0 else None)
+    _check_host(o["info"], "info", lay.n_leaves)
+    prec_id = PREC[prec] if isinstance(prec, str) else int(prec)
+    status = load_library().hps_condense_host(
+        plan.handle, prec_id, _ptr(coef), _ptr(f), int(m), float(tol), int(kmax), _ptr(o.get("S")),
+        _ptr(o["T"]), _ptr(o.get("h")), _ptr(o.get("W")), _ptr(o["info"]), int(chunks), _stream(stream))
+    plan.check(status, "hps_condense_host")
     return o
 
 
