@@ -73,6 +73,8 @@ WORKLOADS = {
                     "(8192), p=24, kappa=400, b=1-0.3sin(4r)cos(6theta), m=1 (seed 4)"),
     "uneven": ("128x80 leaves (10240) of the unit square, p drawn from {12,16,20,24,32} with weights "
                "{.3,.25,.2,.15,.1} (seed 5), kappa=300, b as bumps_p20, m=64 body loads"),
+    "psi_p20": ("the curved domain {(x1, x2/psi(x1))}, psi(z)=1-sin(z)/4, on 64x64 reference leaves (4096), "
+                "p=20, mixed term c12 != 0, b=1, kappa=200, m=1 body load of bumps (seed 6)"),
 }
 
 
@@ -87,7 +89,7 @@ PEAK_SOURCE = {
 def make_workload(name):
     from paper_2211_14969_b300 import workloads as WL
     return {"bumps_p20": WL.bumps_p20, "bumps_p30": WL.bumps_p30, "annulus_p24": WL.annulus_p24,
-            "uneven": WL.uneven}[name]()
+            "uneven": WL.uneven, "psi_p20": WL.psi_p20}[name]()
 
 
 def peaks():

@@ -20,6 +20,11 @@ Workloads (synthetic stand-ins for the paper's experiments, Section 3):
                   to the unit square by r = 1 + x, theta = (pi/2) y; 64 leaves
                   in x (r) and 128 in y (theta); kappa = 400,
                   b = 1 - 0.3 sin(4 r) cos(6 theta), p = 24, m = 1, seed 4.
+* ``psi_p20``     the paper's curved domain Psi = {(x1, x2 / psi(x1))},
+                  psi(z) = 1 - sin(z)/4, over the unit square (mixed term
+                  c12 != 0), b = 1, kappa = 200, p = 20, 64 x 64 leaves,
+                  m = 1 body load of bumps (seed 6), Dirichlet data of the
+                  physical plane wave sin(kappa (0.6 y1 + 0.8 y2)).
 * ``uneven``      128 x 80 leaves of the unit square, p drawn per leaf from
                   {12, 16, 20, 24, 32} with weights {.3, .25, .2, .15, .1},
                   kappa = 300, b as bumps_p20, m = 64 body loads, seed 5.
@@ -70,7 +75,17 @@ class Workload:
         """(6, ...) stack of c11, c12, c22, c1, c2, b at (x, y)."""
         one = xp.ones_like(x)
         zero = xp.zeros_like(x)
-        if self.geometry == "annulus":
+        if self.geometry == "psi":
+            # the curved domain {(x1, x2 / psi(x1))}, psi(z) = 1 - sin(z)/4,
+            # over the reference square (Eq. (parametrization), Eq. (chain_rule))
+            ps = 1.0 - 0.25 * xp.sin(x)
+            dps = -0.25 * xp.cos(x)
+            ddps = 0.25 * xp.sin(x)
+            g = y * dps / ps
+            c11, c12, c22 = one, g, g * g + ps * ps
+            c1, c2 = zero, y * ddps / ps
+            b = one
+        elif self.geometry == "annulus":
             r = 1.0 + x
             th = (math.pi / 2.0) * y
             c11, c12 = one, zero
@@ -103,6 +118,10 @@ class Workload:
     def dirichlet_data(self, x, y, xp=np):
         if self.dirichlet == "planewave":
             return xp.sin(self.kappa * (0.6 * x + 0.8 * y))
+        if self.dirichlet == "psi_planewave":
+            # the plane wave sin(kappa (0.6 y1 + 0.8 y2)) of the physical
+            # domain at (y1, y2) = (x1, x2 / psi(x1))
+            return xp.sin(self.kappa * (0.6 * x + 0.8 * y / (1.0 - 0.25 * xp.sin(x))))
         return xp.zeros_like(x)
 
 
@@ -143,6 +162,19 @@ def annulus(p=24, nx=64, ny=128, kappa=400.0, seed=4, m=1, name=None):
 
 def annulus_p24():
     return annulus()
+
+
+def psi_curved(p=20, nx=64, ny=64, kappa=200.0, seed=6, m=1, name=None):
+    """The paper's curved domain Psi (b = 1) on the reference square: the
+    mixed-derivative coefficient c12 is nonzero; bump loads and the physical
+    plane wave as Dirichlet data."""
+    c, a = _bumps(seed, m)
+    return Workload(name or f"psi_p{p}", nx, ny, kappa, np.full(nx * ny, p, dtype=np.int32), m, seed,
+                    geometry="psi", bcoef="one", dirichlet="psi_planewave", centres=c, amps=a)
+
+
+def psi_p20():
+    return psi_curved()
 
 
 P_SET = (12, 16, 20, 24, 32)

@@ -223,3 +223,21 @@ def test_full_size_grid_reproduces_manufactured_polynomial():
     for us in sols:
         assert rel(us[:, mask], exact[:, mask]) < 1e-9
     assert rel(sols[0][:, mask], sols[1][:, mask]) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_psi_curved_domain_pipeline(prec):
+    """Section 3's curved domain Psi (c12 != 0, corners by extrapolation):
+    condense + merge + solve on 4 x 4 leaves of p = 14 against the oracle's
+    merge tree, and against the exact physical plane wave."""
+    p = 14
+    w = WL.psi_curved(p=p, nx=4, ny=4, kappa=10.0, m=1)
+    w.load = "zero"
+    u_gpu = gpu_pipeline(w, prec)
+    sol, _, _ = oracle_pipeline(w)
+    u_ora = grid_from_sol(sol, p)
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    assert rel(u_gpu[:, mask], u_ora[:, mask]) < (1e-12 if prec == "fp64" else 1e-10)
+    exact = np.stack([w.dirichlet_data(*O.leaf_nodes(p, b)) for b in w.boxes()])
+    assert rel(u_gpu[:, mask], exact[:, mask]) < 1e-9

@@ -45,6 +45,13 @@ def test_annulus_p24_full(prec):
     run_full(WL.annulus_p24(), prec, extra=(0, 8191))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_psi_p20_full(prec):
+    """The paper's curved domain Psi (c12 != 0), 64 x 64 leaves, p = 20,
+    kappa = 200, in one launch at the benchmark size."""
+    run_full(WL.psi_p20(), prec, sample=4, extra=(0, 4095))
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_uneven_full_m64(prec):
     """10240 leaves of five orders and 64 body loads in one launch."""

@@ -231,6 +231,43 @@ def test_leaf_resolve_with_mixed_term_manufactured():
     assert O.relerr(got[ix["I"]], uv[ix["I"]]) < 1e-11
 
 
+def psi_planewave_error(p, n=4, kappa=10.0):
+    """The paper's curved domain Psi (Eq. (parametrization), operator of
+    Eq. (chain_rule), c12 != 0): merged grid solve of n x n leaves with the
+    physical plane wave as Dirichlet data, max error at the interior nodes."""
+    w = WL.psi_curved(p=p, nx=n, ny=n, kappa=kappa, m=1)
+    boxes = O.grid_boxes(n, n)
+    coefs, fs = [], []
+    for b in boxes:
+        x, y = O.leaf_nodes(p, b)
+        coefs.append(w.coefficients(x, y))
+        fs.append(np.zeros((p * p, 1)))
+    sol, _ = hps_grid_solve(p, n, n, coefs, kappa, fs, w.dirichlet_data)
+    ix = O.leaf_index_sets(p)
+    err = 0.0
+    for l, s in enumerate(sol):
+        x, y = O.leaf_nodes(p, boxes[l])
+        err = max(err, float(np.abs(s["u_i"].ravel() - w.dirichlet_data(x, y)[ix["I"]]).max()))
+    return err
+
+
+def test_psi_curved_domain_spectral_convergence():
+    """Section 3's curved domain: with the corner extrapolation the HPS
+    solution converges spectrally to the exact plane wave as p grows."""
+    errs = [psi_planewave_error(p) for p in (6, 10, 14)]
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 1e-10, errs
+
+
+def test_psi_curved_domain_fails_without_corner_reading(monkeypatch):
+    """Dropping the corners (their values taken as zero) leaves an O(1e-2)
+    error that does not decrease with p on the same problem."""
+    real = O.corner_extrapolation
+    monkeypatch.setattr(O, "corner_extrapolation", lambda p: 0.0 * real(p))
+    errs = [psi_planewave_error(p) for p in (10, 14)]
+    assert min(errs) > 1e-3, errs
+
+
 @pytest.mark.parametrize("p,kappa,m", [(6, 3.0, 1), (12, 30.0, 2), (20, 200.0 / 8, 3)])
 def test_leaf_resolve_manufactured(p, kappa, m):
     """Section 2 Remark: re-forming the leaf system and solving with the
