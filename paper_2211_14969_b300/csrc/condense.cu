@@ -326,11 +326,17 @@ __device__ void node_factors(const LeafInfo &L, double kappa2, float *__restrict
 // the x-line and y-line sums run in one loop, eight independent chains
 // sharing the loop.  GENERAL adds the first-derivative and mixed terms
 // (leaf_flags != 0); without them those terms are exactly zero and skipped.
+// The mixed term sum_k Dx[i,k] sum_l Dy[j,l] u(k,l) reaches every node of
+// the leaf; with sep it is evaluated in two passes per chunk, first
+// V(k, j) = sum_l Dy[j,l] u(k,l) for every grid line k (hi and lo planes
+// after Xl in shared memory, p q cwp each) and then sum_k Dx[i,k] V(k, j),
+// 2 p^2 q instead of p^2 q^2 products per column; without sep (the caller's
+// buffer has no room for V) every node sums all p^2 terms itself.
 template <typename T, bool GENERAL, bool RESOLVE = false>
 __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const LeafInfo &L,
                          const float *__restrict__ Dh, const float *__restrict__ Dl,
                          const float *__restrict__ nf, float *__restrict__ Xs, float2 *__restrict__ Dp,
-                         int cw_max, const double *__restrict__ ub = nullptr) {
+                         int cw_max, const double *__restrict__ ub = nullptr, bool sep = false) {
     constexpr int G = 4;
     const int p = L.p, q = L.q, r = L.r, nbd = L.nbd, n = L.n, p2 = p * p;
     for (int e = threadIdx.x; e < 2 * p2; e += NT) Dp[e] = make_float2(Dh[e], Dl[e]);
@@ -346,6 +352,58 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
             Xl[e] = v.y;
         }
         __syncthreads();
+        // the grid function of chunk column cc at node (k, l): X inside, the
+        // unit value of its edge node (condensation) or the edge data (leaf
+        // solve) on the edges, the corner extrapolation at the corners
+        auto U = [&](int k, int l, int cc) -> float2 {
+            const int c = c0 + cc;
+            if (k >= 1 && k <= q && l >= 1 && l <= q) {
+                const int e = ((k - 1) * q + (l - 1)) * cwp + cc;
+                return make_float2(Xh[e], Xl[e]);
+            }
+            if ((k == 0 || k == p - 1) && (l == 0 || l == p - 1)) {
+                // the mean of the extrapolations along the corner's two edges
+                const int o = 2 * p2;
+                const int wl = (l == 0 ? 0 : p), wk = (k == 0 ? 0 : p);
+                const int ev = (k == 0 ? 0 : q), eh = (l == 0 ? 2 * q : 3 * q);   // its W/E and S/N edge
+                if constexpr (RESOLVE) {
+                    DF acc = {0.0f, 0.0f};
+                    for (int t2 = 1; t2 <= q; ++t2) {
+                        const DF a = df_from(ub[(long long)(ev + t2 - 1) * L.m + c]);
+                        const DF b = df_from(ub[(long long)(eh + t2 - 1) * L.m + c]);
+                        df_mac(acc, Dh[o + wl + t2], Dl[o + wl + t2], a.hi, a.lo);
+                        df_mac(acc, Dh[o + wk + t2], Dl[o + wk + t2], b.hi, b.lo);
+                    }
+                    acc = df_norm(acc);
+                    return make_float2(acc.hi, acc.lo);
+                }
+                if (c >= ev && c < ev + q) return make_float2(Dh[o + wl + c - ev + 1], Dl[o + wl + c - ev + 1]);
+                if (c >= eh && c < eh + q) return make_float2(Dh[o + wk + c - eh + 1], Dl[o + wk + c - eh + 1]);
+                return make_float2(0.0f, 0.0f);
+            }
+            if constexpr (RESOLVE) {
+                const DF e = df_from(ub[(long long)edge_index(k, l, p, q) * L.m + c]);
+                return make_float2(e.hi, e.lo);
+            }
+            if (c >= nbd) return make_float2(0.0f, 0.0f);
+            return make_float2(edge_index(k, l, p, q) == c ? 1.0f : 0.0f, 0.0f);
+        };
+        float *Vh = Xl + (long long)n * cwp, *Vl = Vh + (long long)p * q * cwp;
+        const bool two_pass = GENERAL && sep && (L.flags & 1);
+        if (two_pass) {
+            for (int e = threadIdx.x; e < p * q * cw; e += NT) {
+                const int cc = e % cw, kj = e / cw, k = kj / q, j = kj - k * q + 1;
+                DF sk = {0.0f, 0.0f};
+                for (int l = 0; l < p; ++l) {
+                    const float2 u = U(k, l, cc);
+                    df_mac(sk, Dq[j * p + l].x, Dq[j * p + l].y, u.x, u.y);
+                }
+                sk = df_norm(sk);
+                Vh[(long long)kj * cwp + cc] = sk.hi;
+                Vl[(long long)kj * cwp + cc] = sk.lo;
+            }
+            __syncthreads();
+        }
         for (int w = threadIdx.x; w < n * ng; w += NT) {
             const int rr = w / ng, g = w - rr * ng;
             const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
@@ -422,44 +480,19 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                 if (L.flags & 1) {   // mixed derivative: every node of the leaf
 #pragma unroll
                     for (int t = 0; t < G; ++t) {
-                        const int cc = g * G + t, c = c0 + cc;
+                        const int cc = g * G + t;
                         if (cc >= cw) continue;
-                        auto U = [&](int k, int l) -> float2 {
-                            if (k >= 1 && k <= q && l >= 1 && l <= q) {
-                                const int e = ((k - 1) * q + (l - 1)) * cwp + cc;
-                                return make_float2(Xh[e], Xl[e]);
+                        if (two_pass) {
+                            for (int k = 0; k < p; ++k) {
+                                const long long v = ((long long)k * q + (j - 1)) * cwp + cc;
+                                df_mac(axy[t], Dq[i * p + k].x, Dq[i * p + k].y, Vh[v], Vl[v]);
                             }
-                            if ((k == 0 || k == p - 1) && (l == 0 || l == p - 1)) {
-                                // the mean of the extrapolations along the corner's two edges
-                                const int o = 2 * p2;
-                                const int wl = (l == 0 ? 0 : p), wk = (k == 0 ? 0 : p);
-                                const int ev = (k == 0 ? 0 : q), eh = (l == 0 ? 2 * q : 3 * q);   // its W/E and S/N edge
-                                if constexpr (RESOLVE) {
-                                    DF acc = {0.0f, 0.0f};
-                                    for (int t2 = 1; t2 <= q; ++t2) {
-                                        const DF a = df_from(ub[(long long)(ev + t2 - 1) * L.m + c]);
-                                        const DF b = df_from(ub[(long long)(eh + t2 - 1) * L.m + c]);
-                                        df_mac(acc, Dh[o + wl + t2], Dl[o + wl + t2], a.hi, a.lo);
-                                        df_mac(acc, Dh[o + wk + t2], Dl[o + wk + t2], b.hi, b.lo);
-                                    }
-                                    acc = df_norm(acc);
-                                    return make_float2(acc.hi, acc.lo);
-                                }
-                                if (c >= ev && c < ev + q) return make_float2(Dh[o + wl + c - ev + 1], Dl[o + wl + c - ev + 1]);
-                                if (c >= eh && c < eh + q) return make_float2(Dh[o + wk + c - eh + 1], Dl[o + wk + c - eh + 1]);
-                                return make_float2(0.0f, 0.0f);
-                            }
-                            if constexpr (RESOLVE) {
-                                const DF e = df_from(ub[(long long)edge_index(k, l, p, q) * L.m + c]);
-                                return make_float2(e.hi, e.lo);
-                            }
-                            if (c >= nbd) return make_float2(0.0f, 0.0f);
-                            return make_float2(edge_index(k, l, p, q) == c ? 1.0f : 0.0f, 0.0f);
-                        };
+                            continue;
+                        }
                         for (int k = 0; k < p; ++k) {
                             DF sk = {0.0f, 0.0f};
                             for (int l = 0; l < p; ++l) {
-                                const float2 u = U(k, l);
+                                const float2 u = U(k, l, cc);
                                 df_mac(sk, Dq[j * p + l].x, Dq[j * p + l].y, u.x, u.y);
                             }
                             sk = df_norm(sk);
@@ -735,8 +768,19 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             // chunk buffers hold (they are idle between eliminations)
             // the D/D^2 pairs take the front of the buffer, X chunks the rest
             const int dpairs = 2 * L.p * L.p;
-            const int xs_cap = (int)(((size_t)NB * (ldp + Cfg<T, NB>::CH) * sizeof(T) / sizeof(float2) - dpairs) / L.n);
-            const int xs_cols = xs_cap >= 16 ? 16 : xs_cap >= 8 ? 8 : 4;
+            const long long buf2 = (long long)((size_t)NB * (ldp + Cfg<T, NB>::CH) * sizeof(T) / sizeof(float2)) - dpairs;
+            const int xs_cap = (int)(buf2 / L.n);
+            int xs_cols = xs_cap >= 16 ? 16 : xs_cap >= 8 ? 8 : 4;
+            // with the mixed term, the grid-line sums V take p q pairs a column
+            // beside X's n when the buffer holds at least 4 such columns
+            bool sep = false;
+            if (L.flags & 1) {
+                const int cap2 = (int)(buf2 / (L.n + L.p * L.q));
+                if (cap2 >= 4) {
+                    sep = true;
+                    xs_cols = cap2 >= 16 ? 16 : cap2 >= 8 ? 8 : 4;
+                }
+            }
             for (int i = threadIdx.x >> 5; i < L.n; i += NWARP)
                 for (int c = threadIdx.x & 31; c < L.r; c += 32)
                     X[(long long)i * L.r + c] = make_float2((float)M[(long long)i * L.LDC + L.n4 + c], 0.0f);
@@ -751,8 +795,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                 bool done = false;
                 while (!done && it < P.kmax) {
                     float *xs = (float *)((float2 *)sm.Ps + 2 * L.p * L.p);
-                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl);
-                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
+                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl, sep);
+                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, sep);
                     else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
                     __syncthreads();
                     lu_solve<T, NB, 0, INV>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
