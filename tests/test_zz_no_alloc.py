@@ -52,11 +52,13 @@ class _Leaves:
         return self.box
 
 
-@pytest.mark.parametrize("which", ["p12_8x8", "p20_bench_leaves"])
+@pytest.mark.parametrize("which", ["p12_8x8", "p20_bench_leaves", "psi_p14_4x4"])
 def test_noalloc_matches_plan_path_two_calls(which):
     lib = hps.load_library()
     if which == "p12_8x8":
         w = WL.bumps(p=12, nx=8, ny=8, kappa=60.0, seed=13, m=1)
+    elif which == "psi_p14_4x4":   # mixed term c12 != 0: the corner weights of the scratch tables
+        w = WL.psi_curved(p=14, nx=4, ny=4, kappa=10.0, m=1)
     else:   # 40 leaves of the 64 x 64, p = 20, kappa = 200 workload
         w = _Leaves(WL.bumps_p20(), 40)
     p = int(w.p[0])
