@@ -290,6 +290,29 @@ def cpu_baseline(w, budget_s, sample_cap=None, seed=1234):
     return rec, results
 
 
+def merge_cpu_baseline(w, n_sub=8):
+    """The oracle's merge tree as it stands on the n_sub x n_sub leaves at
+    the corner of the grid (leaf maps condensed by the oracle beforehand,
+    not timed): algorithmic merge GFLOP/s of that sub-grid."""
+    import oracle.hps_oracle as O
+    p = int(w.p[0])
+    boxes = w.boxes()
+    leaves = []
+    for ix in range(n_sub):
+        for iy in range(n_sub):
+            b = boxes[ix * w.ny + iy]
+            x, y = O.leaf_nodes(p, b)
+            f = w.body_load(x, y).reshape(p * p, -1) if w.m > 0 else None
+            leaves.append(O.condense_leaf(p, b, w.coefficients(x, y), w.kappa, f))
+    t0 = time.perf_counter()
+    O.hps_upward(p, n_sub, n_sub, leaves)
+    dt = time.perf_counter() - t0
+    gf, _ = merge_flops(p - 2, n_sub, n_sub, max(w.m, 1))
+    return {"value": gf / dt / 1e9, "unit": "GFLOP/s (algorithmic, merge)", "kind": "oracle",
+            "sample": f"hps_upward of the oracle on the {n_sub}x{n_sub} corner leaves ({gf / 1e9:.2f} Gflop in "
+                      f"{dt:.2f} s), numpy/LAPACK FP64"}
+
+
 def parity_vs_oracle(w, lay, outs, results):
     """Max per-leaf relative error of GPU outputs against the oracle leaves."""
     worst = {}
@@ -550,6 +573,9 @@ def run_gpu(args, rank, ws):
                 "cpu_baseline": cpu,
                 "parity_vs_oracle_sampled": parity}
         if reduced is not None:
+            if ws == 1 and not args.no_cpu_baseline:
+                reduced["cpu_baseline"] = merge_cpu_baseline(w)
+                reduced["cpu_baseline"]["cores"] = cpu["cores"] if cpu else 1
             line["reduced_solve_fp64"] = reduced
         if per_order is not None:
             line["per_order_launches"] = per_order

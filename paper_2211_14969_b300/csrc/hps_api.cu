@@ -130,6 +130,7 @@ struct hps_plan {
     int merge_nx = 0, merge_ny = 0, merge_m = -1;
     bool merged = false;
     int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
+    SplitAux split_aux{nullptr, nullptr, nullptr};   // look-ahead stream and events, made on first use
     // hps_condense_host: device copies of the inputs and outputs, the chunk
     // work-queue orders and counters, two more streams and their events
     DevBuf hstage, horder;
@@ -784,7 +785,12 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         D.info = (int *)L.info.p;
         D.ipiv = split ? (int *)L.piv.p : nullptr;
         D.u3 = (double *)L.u3.p;
-        if ((e = launch_merge_level(D, !root, s)) != cudaSuccess) break;
+        if (split && P->split_aux.side == nullptr) {
+            if ((e = cudaStreamCreateWithFlags(&P->split_aux.side, cudaStreamNonBlocking)) != cudaSuccess) break;
+            if ((e = cudaEventCreateWithFlags(&P->split_aux.a, cudaEventDisableTiming)) != cudaSuccess) break;
+            if ((e = cudaEventCreateWithFlags(&P->split_aux.b, cudaEventDisableTiming)) != cudaSuccess) break;
+        }
+        if ((e = launch_merge_level(D, !root, s, split ? &P->split_aux : nullptr)) != cudaSuccess) break;
     }
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_merge");
     if ((e = P->u_leaf.ensure((size_t)P->n_leaves * 4 * q * std::max(m, 1) * sizeof(double))) != cudaSuccess)
@@ -796,7 +802,7 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
     P->launches = 0;
     for (auto &L : P->levels) {
         const int steps = (L.dev.n3 + 15) / 16;
-        P->launches += 1 + (L.dev.Th ? 1 : 0) + (L.dev.ipiv ? 5 * steps - 2 : 1);
+        P->launches += 1 + (L.dev.Th ? 1 : 0) + (L.dev.ipiv ? 6 * steps - 3 : 1);
     }
     return HPS_OK;
 }
@@ -846,8 +852,10 @@ void hps_destroy(hps_plan *P) {
     P->u_leaf.release();
     P->hstage.release();
     P->horder.release();
-    for (cudaStream_t t : {P->hs_comp, P->hs_h2d, P->hs_d2h})
+    for (cudaStream_t t : {P->hs_comp, P->hs_h2d, P->hs_d2h, P->split_aux.side})
         if (t) cudaStreamDestroy(t);
+    for (cudaEvent_t ev : {P->split_aux.a, P->split_aux.b})
+        if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : P->hev) cudaEventDestroy(ev);
     P->work.release();
     P->tables.release();

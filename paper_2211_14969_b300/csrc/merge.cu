@@ -209,7 +209,7 @@ __global__ void leaf_recover(int p, int m, const double *__restrict__ S, const d
 
 }  // namespace
 
-cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s) {
+cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s, const SplitAux *aux) {
     const int C = L.c3 + L.np + L.m;
     long long work = (long long)L.n3 * C;
     int gx = (int)((work + NT - 1) / NT);
@@ -218,7 +218,7 @@ cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStr
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (L.ipiv)
-        e = launch_split_solve(L, L.ipiv, s);
+        e = launch_split_solve(L, L.ipiv, s, aux);
     else
         e = launch_dense_solve(L.aug, (long long)L.n3 * L.lda, L.n3, L.c3, C, L.lda, L.nm, L.info, s);
     if (e != cudaSuccess) return e;

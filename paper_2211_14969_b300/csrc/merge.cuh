@@ -28,12 +28,19 @@ struct MergeLevelDev {
     double *u3;                      // [nm][n3][m] shared-edge values of the downward pass
 };
 
-cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s);
+// A second stream and two events for the look-ahead of the split solve.
+struct SplitAux {
+    cudaStream_t side;
+    cudaEvent_t a, b;
+};
+
+cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s,
+                               const SplitAux *aux = nullptr);
 // [Z | 0 | B] -> [U | 0 | X] for every merge of a level, one blocked-LU step
 // per launch with each step spread over many CTAs (merge_split.cu).  Needs
 // L.ipiv; cudaErrorInvalidValue when the panel of n3 rows does not fit
 // shared memory (split_solve_fits).
-cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s);
+cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s, const SplitAux *aux = nullptr);
 bool split_solve_fits(int n3);
 cudaError_t launch_merge_down(const MergeLevelDev &L, const double *upar, double *uchild, cudaStream_t s);
 cudaError_t launch_leaf_recover(int n_leaves, int p, int m, const double *S, const double *W,

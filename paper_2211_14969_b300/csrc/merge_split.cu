@@ -17,7 +17,9 @@
 //     swap_lower: apply the panel's interchanges to the columns right of the
 //                 panel and solve the unit-lower L11 for the NB rows at k
 //                 (one thread per column);
-//     gemm:       A22 -= L21 U12 over 64 x 64 tiles;
+//     gemm:       A22 -= L21 U12 over 64 x 64 tiles, the next panel's
+//                 columns first and the rest on a second stream, where it
+//                 overlaps the next panel's factorization;
 //   then for each block row kb from the bottom:
 //     upper:      X1 = U11^{-1} Y1 on the NB rows at kb (thread per column);
 //     gemm:       Y0 -= U01 X1 on the rows above.
@@ -246,7 +248,7 @@ constexpr int kSplitNB = 16;
 
 bool split_solve_fits(int n3) { return (size_t)((n3 | 1) * kSplitNB) * sizeof(double) <= 200 * 1024; }
 
-cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t st) {
+cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t st, const SplitAux *aux) {
     constexpr int NB = kSplitNB;
     const int n3 = L.n3, lda = L.lda, nm = L.nm;
     const int C = L.c3 + L.np + L.m;
@@ -256,26 +258,46 @@ cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s
     cudaError_t e = cudaFuncSetAttribute(split_panel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(L.info, 0, (size_t)nm * sizeof(int), st)) != cudaSuccess) return e;
+    auto gemm = [&](cudaStream_t s, int r0, int nr, int c0, int nc, int ka, int kb, int K) {
+        split_gemm<NB><<<dim3((nc + GT - 1) / GT, (nr + GT - 1) / GT, nm), 256, 0, s>>>(L.aug, stride, lda, r0, nr, c0,
+                                                                                        nc, ka, kb, K);
+    };
+    // With aux, look-ahead: each step first updates only the next panel's
+    // columns, and the rest of its trailing update runs on the side stream
+    // while the next panel is factored (the two touch disjoint columns); the
+    // next step's interchanges wait for it.
+    bool pending = false;
     for (int k = 0; k < n3; k += NB) {
         const int nbk = n3 - k < NB ? n3 - k : NB;
         const size_t sm = (size_t)(((n3 - k) | 1) * NB) * sizeof(double);
         split_panel<NB><<<nm, PNT, sm, st>>>(L.aug, stride, n3, lda, k, nbk, ipiv, L.info);
+        if (pending && (e = cudaStreamWaitEvent(st, aux->b, 0)) != cudaSuccess) return e;
+        pending = false;
         const int cr = C - (k + nbk);
         if (cr > 0) split_swap_lower<NB><<<dim3((cr + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, k, nbk, C, ipiv);
         const int nr = n3 - (k + nbk);
-        if (nr > 0 && cr > 0)
-            split_gemm<NB><<<dim3((cr + GT - 1) / GT, (nr + GT - 1) / GT, nm), 256, 0, st>>>(
-                L.aug, stride, lda, k + nbk, nr, k + nbk, cr, k, k, nbk);
+        if (nr > 0 && cr > 0) {
+            const int next_w = nr < NB ? nr : NB;
+            if (aux && cr > next_w) {
+                gemm(st, k + nbk, nr, k + nbk, next_w, k, k, nbk);
+                if ((e = cudaEventRecord(aux->a, st)) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(aux->side, aux->a, 0)) != cudaSuccess) return e;
+                gemm(aux->side, k + nbk, nr, k + nbk + next_w, cr - next_w, k, k, nbk);
+                if ((e = cudaEventRecord(aux->b, aux->side)) != cudaSuccess) return e;
+                pending = true;
+            } else {
+                gemm(st, k + nbk, nr, k + nbk, cr, k, k, nbk);
+            }
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (pending && (e = cudaStreamWaitEvent(st, aux->b, 0)) != cudaSuccess) return e;
     const int nrhs = C - L.c3;
     const int last = ((n3 - 1) / NB) * NB;
     for (int kb = last; kb >= 0; kb -= NB) {
         const int nbk = n3 - kb < NB ? n3 - kb : NB;
         split_upper<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, lda, kb, nbk, L.c3, C);
-        if (kb > 0)
-            split_gemm<NB><<<dim3((nrhs + GT - 1) / GT, (kb + GT - 1) / GT, nm), 256, 0, st>>>(
-                L.aug, stride, lda, 0, kb, L.c3, nrhs, kb, kb, nbk);
+        if (kb > 0) gemm(st, 0, kb, L.c3, nrhs, kb, kb, nbk);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
