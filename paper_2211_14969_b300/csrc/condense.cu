@@ -187,11 +187,6 @@ __device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restri
                 row[(k - 1) * q + (l - 1)] = v;
                 return;
             }
-            if (dense) {
-                // the two corners at the ends of this node's edge
-                if (bk) v += cw[l] * entry(k, 0) + cw[p + l] * entry(k, p - 1);
-                else v += cw[k] * entry(0, l) + cw[p + k] * entry(p - 1, l);
-            }
             row[L.n4 + edge_index(k, l, p, q)] = -v;
         };
         if (!dense) {
@@ -200,8 +195,35 @@ __device__ void assemble(T *__restrict__ M, const LeafInfo &L, const T *__restri
                 else if (t - p != j) put(i, t - p);         // the y-line, diagonal already written
             }
         } else {
-            for (int k = 0; k < p; ++k)
-                for (int l = lane; l < p; l += 32) put(k, l);
+            // every node: the mixed term is the outer product of
+            // a_k = axy Dx[i,k] and Dy[j,l]; the line terms and the corner
+            // entries (mixed only) are formed once per line / per row
+            const T *Dyj = Dw + j * p;
+            const T a0 = axy * Dw[i * p], aP = axy * Dw[i * p + p - 1];
+            const T c00 = -(a0 * Dyj[0]), c0P = -(a0 * Dyj[p - 1]);
+            const T cP0 = -(aP * Dyj[0]), cPP = -(aP * Dyj[p - 1]);
+            for (int k = 0; k < p; ++k) {
+                const T ak = axy * Dw[i * p + k];
+                const T xk = ax2 * D2w[i * p + k] + ax1 * Dw[i * p + k];   // x-line entry at column j
+                const bool bk = (k == 0 || k == p - 1);
+                for (int l = lane; l < p; l += 32) {
+                    const bool bl = (l == 0 || l == p - 1);
+                    if (bk && bl) continue;   // corners are not unknowns
+                    T v = ak * Dyj[l];
+                    if (l == j) v += xk;
+                    if (k == i) v += ay2 * D2w[j * p + l] + ay1 * Dw[j * p + l];
+                    v = -v;
+                    if (k == i && l == j) v -= dg;
+                    if (!bk && !bl) {
+                        row[(k - 1) * q + (l - 1)] = v;
+                    } else {
+                        // the two corners at the ends of this node's edge
+                        if (bk) v += cw[l] * (k == 0 ? c00 : cP0) + cw[p + l] * (k == 0 ? c0P : cPP);
+                        else v += cw[k] * (l == 0 ? c00 : c0P) + cw[p + k] * (l == 0 ? cP0 : cPP);
+                        row[L.n4 + edge_index(k, l, p, q)] = -v;
+                    }
+                }
+            }
         }
         if (L.f)
             for (int c = lane; c < L.m; c += 32) row[nA + c] = cvt(L.f[(long long)node * L.m + c]);
