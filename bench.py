@@ -95,8 +95,9 @@ def make_workload(name):
 def peaks():
     """Roofline denominators: FP32 and FP64 ALU peaks from unit counts and the
     maximum SM clock (148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz); FP64 is
-    the nominal 1.25 TFLOP/s of the part.  HBM from the driver's measurement
-    when present."""
+    the nominal 1.25 TFLOP/s of the part.  HBM and BF16 from the measured
+    peaks file (a STREAM-style copy and a BF16 GEMM on this part) when
+    present."""
     sm_mhz = 2032.0
     hbm = None
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
