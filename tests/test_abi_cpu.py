@@ -85,6 +85,9 @@ def test_null_plan_calls_are_argument_errors(lib):
     assert lib.hps_leaf_nodes(None, vp(1), None) == hps.HPS_ERR_ARG
     assert lib.hps_leaf_resolve(None, 0, vp(1), None, 1, vp(1), 0.0, 0, vp(1), vp(1), None) == hps.HPS_ERR_ARG
     assert lib.hps_leaf_recover(None, vp(1), None, 1, vp(1), vp(1), None) == hps.HPS_ERR_ARG
+    assert lib.hps_condense_host(None, 0, vp(1), None, 0, 0.0, 0, None, vp(1), None, None, vp(1), 0,
+                                 None) == hps.HPS_ERR_ARG
+    assert lib.hps_set_merge_split(None, -1) == hps.HPS_ERR_ARG
     assert lib.hps_set_timing(None, 1) == hps.HPS_ERR_ARG
     assert lib.hps_last_launch_count(None) == 0
     lib.hps_destroy(None)   # no-op
