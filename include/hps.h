@@ -28,11 +28,14 @@
  *  - All pointers named d_* are device pointers on the current CUDA device,
  *    owned by the caller, and must stay valid until the stream reaches the
  *    work that reads or writes them.  Host pointers are read before the call
- *    returns.  Every call is asynchronous on the given stream (NULL = legacy
- *    default stream) and reports argument and launch errors synchronously.
+ *    returns, except the h_* buffers of hps_condense_host, which are copied
+ *    asynchronously and must stay valid until the stream reaches the end of
+ *    that call.  Every call is asynchronous on the given stream (NULL =
+ *    legacy default stream) and reports argument and launch errors
+ *    synchronously.
  *  - No call allocates or frees a caller buffer.  A plan owns its device
- *    workspace (allocated at build time, grown on demand by hps_condense and
- *    hps_merge, freed by hps_destroy).
+ *    workspace (allocated at build time, grown on demand by hps_condense,
+ *    hps_condense_host and hps_merge, freed by hps_destroy).
  *  - A plan is not thread-safe; use one plan per host thread or serialise.
  */
 #ifndef HPS_H
