@@ -242,6 +242,41 @@ __global__ void __launch_bounds__(256) split_gemm(double *__restrict__ aug, long
     }
 }
 
+// The same update for a block at most 16 columns wide (the next panel's
+// columns in the look-ahead): 64 x 16 tiles, 4 outputs per thread.
+template <int KM>
+__global__ void __launch_bounds__(256) split_gemm_n16(double *__restrict__ aug, long long stride, int lda, int r0,
+                                                      int nr, int c0, int nc, int ka, int kb, int K) {
+    __shared__ double As[KM][GT + 1];
+    __shared__ double Bs[KM][16];
+    const int s = blockIdx.z;
+    double *A = aug + (long long)s * stride;
+    const int tr = blockIdx.y * GT;
+    for (int e = threadIdx.x; e < GT * KM; e += 256) {
+        const int i = e / KM, t = e % KM;
+        As[t][i] = (tr + i < nr && t < K) ? A[(long long)(r0 + tr + i) * lda + ka + t] : 0.0;
+    }
+    for (int e = threadIdx.x; e < KM * 16; e += 256) {
+        const int t = e / 16, j = e % 16;
+        Bs[t][j] = (t < K && j < nc) ? A[(long long)(kb + t) * lda + c0 + j] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // outputs (ty + 16u, tx)
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int t = 0; t < KM; ++t) {
+        const double b = Bs[t][tx];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(As[t][ty + 16 * u], b, acc[u]);
+    }
+    if (tx >= nc) return;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = tr + ty + 16 * u;
+        if (i < nr) A[(long long)(r0 + i) * lda + c0 + tx] -= acc[u];
+    }
+}
+
 }  // namespace
 
 constexpr int kSplitNB = 16;
@@ -279,7 +314,8 @@ cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s
         if (nr > 0 && cr > 0) {
             const int next_w = nr < NB ? nr : NB;
             if (aux && cr > next_w) {
-                gemm(st, k + nbk, nr, k + nbk, next_w, k, k, nbk);
+                split_gemm_n16<NB><<<dim3(1, (nr + GT - 1) / GT, nm), 256, 0, st>>>(L.aug, stride, lda, k + nbk, nr,
+                                                                                    k + nbk, next_w, k, k, nbk);
                 if ((e = cudaEventRecord(aux->a, st)) != cudaSuccess) return e;
                 if ((e = cudaStreamWaitEvent(aux->side, aux->a, 0)) != cudaSuccess) return e;
                 gemm(aux->side, k + nbk, nr, k + nbk + next_w, cr - next_w, k, k, nbk);
