@@ -17,9 +17,9 @@
 //     swap_lower: apply the panel's interchanges to the columns right of the
 //                 panel and solve the unit-lower L11 for the NB rows at k
 //                 (one thread per column);
-//     gemm:       A22 -= L21 U12 over 64 x 64 tiles, the next panel's
-//                 columns first and the rest on a second stream, where it
-//                 overlaps the next panel's factorization;
+//     gemm:       A22 -= L21 U12, the next panel's columns first (64 x 16
+//                 tiles) and the rest (64 x 64 tiles) on a second stream,
+//                 where it overlaps the next panel's factorization;
 //   then for each block row kb from the bottom:
 //     upper:      X1 = U11^{-1} Y1 on the NB rows at kb (thread per column);
 //     gemm:       Y0 -= U01 X1 on the rows above.
