@@ -267,13 +267,15 @@ hps_status hps_phase_times(hps_plan *plan, float *ms, int n);
  * device array inside the library, held by every GPU that loads the library
  * until the process exits.  A call whose tables plus one leaf's workspace
  * ((p-2)^2 x (round4((p-2)^2) + 4(p-2) + m) doubles) do not fit is rejected
- * with HPS_ERR_ARG; a smaller fit means fewer leaves in flight.  The first
- * call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * with HPS_ERR_ARG; a smaller fit means fewer leaves in flight.  Every call
+ * looks up the array's device address in the current context
+ * (cudaGetSymbolAddress), so the entry point stays valid after
+ * cudaDeviceReset; the first call on a device also loads the library's
+ * device code there and should come before any stream capture.  All
  * calls on a device share the array: calls that overlap on the GPU (on
  * different streams, or from different host threads without ordering) race
  * and corrupt each other's results.  Errors: HPS_ERR_ARG / HPS_ERR_CUDA, with
- * the message in hps_last_error(NULL). */
+ * the message in hps_last_error(NULL) of the calling thread. */
 hps_status hps_condense_noalloc(int n_leaves, int p, double kappa, const double *d_box,
                                 const double *d_coef, const double *d_f, int m, double *d_S,
                                 double *d_T, double *d_h, double *d_W, int *d_info, hps_stream stream);
@@ -281,8 +283,9 @@ hps_status hps_condense_noalloc(int n_leaves, int p, double kappa, const double 
 /* Number of kernel launches enqueued by the last hps_condense call. */
 int hps_last_launch_count(const hps_plan *plan);
 
-/* Last error message of this plan (or of the last failed build when plan
- * is NULL); never NULL. */
+/* Last error message of this plan, or, when plan is NULL, of the last
+ * failed call without a plan (hps_build_leaves, hps_condense_noalloc) made
+ * by the calling host thread (the message is kept per thread); never NULL. */
 const char *hps_last_error(const hps_plan *plan);
 
 /* Free the plan and its workspace (synchronises the device first). */

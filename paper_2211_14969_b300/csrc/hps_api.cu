@@ -18,7 +18,10 @@ using namespace hps;
 
 namespace {
 
-std::string g_build_error;  // message of the last failed hps_build_leaves
+// Message of the last failed call without a plan (hps_build_leaves,
+// hps_condense_noalloc) on this host thread: thread_local, so threads that
+// fail at the same time do not race on it.
+thread_local std::string g_build_error;
 
 struct DevBuf {
     void *p = nullptr;

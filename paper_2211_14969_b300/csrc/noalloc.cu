@@ -16,7 +16,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "hps.h"
@@ -37,25 +36,15 @@ using namespace hps;
 constexpr size_t kScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Device address of the scratch array on the current device (host code must
-// not use g_scratch itself: on the host it is only a stand-in symbol).
-cudaError_t scratch_address(int dev, void **out) {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (g_scratch_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
-    return cudaSuccess;
-}
+// Device address of the scratch array in the current device's context (host
+// code must not use g_scratch itself: on the host it is only a stand-in
+// symbol).  Looked up on every call rather than cached: a cached address
+// would dangle once cudaDeviceReset or a re-created primary context reloads
+// the module.  After the first call on a device (which loads the module)
+// the lookup is a host-side table query.
+cudaError_t scratch_address(void **out) { return cudaGetSymbolAddress(out, g_scratch); }
 
 // Per-call set-up in the scratch: uniform-p leaf tables (order p, packed
 // offsets, identity work order), the Chebyshev matrix D of order p on
@@ -160,9 +149,8 @@ extern "C" hps_status hps_condense_noalloc(int n_leaves, int p, double kappa, co
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(HPS_ERR_CUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(HPS_ERR_ARG, "device ordinal out of range");
     void *base_v = nullptr;
-    e = scratch_address(dev, &base_v);
+    e = scratch_address(&base_v);
     if (e != cudaSuccess) return fail(HPS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     unsigned char *base = (unsigned char *)base_v;
     const LuBlocking blk = choose_blocking(HPS_FP64, (int)n, p);

@@ -59,20 +59,81 @@ def relerr(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
-def compare_leaves(w, plan, out, leaves, tol_fp64, cond_factor=10.0, coef_fn=None, load_fn=None):
+# Interior blocks more ill-conditioned than this belong to leaves near an
+# interior Dirichlet resonance.  Two correct FP64 eliminations of the same
+# system (other pivot or summation order) may differ by about
+# cond(A_ii) eps; above cond = 1e5 the bound 10 cond eps exceeds 2e-10, more
+# than even the mixed path's bar.  Only such leaves get the cond term in
+# their bar, and they are reported separately; every other leaf is held to
+# the fixed bar (1e-12 on the FP64 path, 1e-10 on the mixed paths).  Of the
+# full-size workloads, bumps_p20 has none (cond <= 5.2e3), bumps_p30 12 of
+# 1024 (tests/golden/worst_cond_leaves.json).
+COND_FLAG = 1e5
+
+
+def leaf_bar(tol, cond, cond_factor=10.0):
+    """(bar, flagged) of one leaf: the fixed bar, or for a near-resonant
+    leaf (cond(A_ii) > COND_FLAG) max(tol, cond_factor cond eps)."""
+    if cond > COND_FLAG:
+        return max(tol, cond_factor * cond * EPS), True
+    return tol, False
+
+
+def _oracle_outputs(w, l, coef_fn=None, load_fn=None):
+    ref = oracle_leaf(w, l, coef_fn, load_fn)
+    cond = float(np.linalg.cond(ref["A_ii"]))
+    return {k: ref[k] for k in ("S", "T", "W", "h") if k in ref}, cond
+
+
+def _oracle_job(args):
+    w, l = args
+    return l, _oracle_outputs(w, l)
+
+
+def _one_blas_thread():
+    import os
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    try:
+        from threadpoolctl import threadpool_limits
+        threadpool_limits(1)
+    except Exception:
+        pass
+
+
+def oracle_pool(workers=None):
+    """A pool of spawned processes (one BLAS thread each) for the oracle's
+    per-leaf work; spawned, not forked, since the parent holds a CUDA
+    context."""
+    import multiprocessing as mp
+    import os
+    # read by the workers when they import numpy (set before they start)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    return mp.get_context("spawn").Pool(workers or max(1, min(32, os.cpu_count() or 1)),
+                                        initializer=_one_blas_thread)
+
+
+def compare_leaves(w, plan, out, leaves, tol, cond_factor=10.0, coef_fn=None, load_fn=None, pool=None):
     """Per-leaf relative Frobenius errors of every output against the oracle.
 
-    The bar for a leaf is max(tol, cond_factor * cond(A_ii) * eps): two
-    correct FP64 eliminations of the same system with different pivoting or
-    summation order may differ by about cond * eps.  Returns the records."""
+    The bar of a leaf is the fixed tol, or max(tol, cond_factor cond(A_ii)
+    eps) when its interior block is near-resonant (leaf_bar).  With a pool
+    (oracle_pool; only for workloads without custom coefficient or load
+    functions) the oracle leaves are computed in parallel.  Returns the
+    records."""
     recs = []
     cpu = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    leaves = [int(l) for l in leaves]
+    if pool is not None and coef_fn is None and load_fn is None:
+        refs = dict(pool.map(_oracle_job, [(w, l) for l in leaves]))
+    else:
+        refs = {l: _oracle_outputs(w, l, coef_fn, load_fn) for l in leaves}
     for l in leaves:
-        ref = oracle_leaf(w, l, coef_fn, load_fn)
+        ref, cond = refs[l]
         got = leaf_slices(plan.layout, cpu, l, w.m)
-        cond = np.linalg.cond(ref["A_ii"])
-        bar = max(tol_fp64, cond_factor * cond * EPS)
-        rec = {"leaf": l, "cond": cond, "bar": bar}
+        bar, flagged = leaf_bar(tol, cond, cond_factor)
+        rec = {"leaf": l, "cond": cond, "bar": bar, "flagged": flagged}
         for k in ("S", "T", "W", "h"):
             if k in got and k in ref:
                 rec[k] = relerr(got[k], ref[k])
@@ -81,5 +142,17 @@ def compare_leaves(w, plan, out, leaves, tol_fp64, cond_factor=10.0, coef_fn=Non
 
 
 def assert_within(recs):
-    bad = [r for r in recs if any(r[k] > r["bar"] for k in ("S", "T", "W", "h") if k in r)]
+    """Every output of every leaf within its bar; near-resonant leaves (the
+    ones whose bar carries the cond term) are printed separately."""
+    outs = ("S", "T", "W", "h")
+    flagged = [r for r in recs if r.get("flagged")]
+    plain = [r for r in recs if not r.get("flagged")]
+    if plain:
+        worst = {k: max(r[k] for r in plain if k in r) for k in outs if any(k in r for r in plain)}
+        print(f"{len(plain)} leaves at the fixed bar {plain[0]['bar']:.0e}: max errors "
+              + ", ".join(f"{k} {v:.1e}" for k, v in worst.items()))
+    for r in flagged:
+        print(f"near-resonant leaf {r['leaf']}: cond(A_ii) {r['cond']:.2e}, bar {r['bar']:.1e}, errors "
+              + ", ".join(f"{k} {r[k]:.1e}" for k in outs if k in r))
+    bad = [r for r in recs if any(r[k] > r["bar"] for k in outs if k in r)]
     assert not bad, bad[:3]
