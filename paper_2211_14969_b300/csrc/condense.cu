@@ -614,12 +614,24 @@ __device__ void write_outputs_df(const CondenseParams &P, int leaf, const LeafIn
     const int q = L.q, p = L.p, n = L.n, nbd = L.nbd, m = L.m, r = L.r;
     double *S = P.S ? P.S + P.lt.o_sb[leaf] : nullptr;
     double *W = (P.W && m > 0) ? P.W + P.lt.o_ni[leaf] * m : nullptr;
-    for (int i = warp; i < n; i += NWARP) {
-        const float2 *xr = X + (long long)i * r;
-        if (S)
-            for (int b = lane; b < nbd; b += 32) S[(long long)i * nbd + b] = f2d(xr[b].x) + f2d(xr[b].y);
-        if (W)
-            for (int cc = lane; cc < m; cc += 32) W[(long long)i * m + cc] = f2d(xr[nbd + cc].x) + f2d(xr[nbd + cc].y);
+    {   // S and W: X row by row, eight loads in flight per thread
+        const int nr = n * r;
+        for (int e0 = threadIdx.x; e0 < nr; e0 += 8 * NT) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = e0 + u * NT < nr ? X[e0 + u * NT] : make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * NT, i = e / r, b = e - i * r;
+                if (e >= nr) continue;
+                const double x = f2d(v[u].x) + f2d(v[u].y);
+                if (b < nbd) {
+                    if (S) S[(long long)i * nbd + b] = x;
+                } else if (W) {
+                    W[(long long)i * m + (b - nbd)] = x;
+                }
+            }
+        }
     }
     double *Tm = P.T + P.lt.o_bb[leaf];
     double *hm = (m > 0 && P.h) ? P.h + P.lt.o_nb[leaf] * m : nullptr;
@@ -685,20 +697,36 @@ __device__ bool refine_update(T *__restrict__ M, float2 *__restrict__ X, float *
     const int r = L.r;
     for (int c = threadIdx.x; c < 2 * r; c += NT) colmax[c] = 0u;
     __syncthreads();
+    constexpr int UB = 8;   // rows whose loads are all issued before the first is used
     for (int c0 = 0; c0 < r; c0 += 32) {
         const int c = c0 + lane;
         float dmax = 0.0f, xmax = 0.0f;
         if (c < r) {
-            for (int i = warp; i < L.n; i += NWARP) {
-                const float d = (float)M[(long long)i * L.LDC + L.n4 + c];
-                const float2 x = X[(long long)i * r + c];
-                float s, e;
-                two_sum(x.x, d, s, e);
-                const float lo = __fadd_rn(x.y, e);
-                const float hi = __fadd_rn(s, lo);   // renormalise: |lo| well below ulp(s)
-                X[(long long)i * r + c] = make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
-                dmax = fmaxf(dmax, fabsf(d));
-                xmax = fmaxf(xmax, fabsf(hi));
+            for (int i0 = warp; i0 < L.n; i0 += NWARP * UB) {
+                float dv[UB];
+                float2 xv[UB];
+#pragma unroll
+                for (int u = 0; u < UB; ++u) {
+                    const int i = i0 + u * NWARP;
+                    if (i < L.n) {
+                        dv[u] = (float)M[(long long)i * L.LDC + L.n4 + c];
+                        xv[u] = X[(long long)i * r + c];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UB; ++u) {
+                    const int i = i0 + u * NWARP;
+                    if (i >= L.n) continue;
+                    const float d = dv[u];
+                    const float2 x = xv[u];
+                    float s, e;
+                    two_sum(x.x, d, s, e);
+                    const float lo = __fadd_rn(x.y, e);
+                    const float hi = __fadd_rn(s, lo);   // renormalise: |lo| well below ulp(s)
+                    X[(long long)i * r + c] = make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s)));
+                    dmax = fmaxf(dmax, fabsf(d));
+                    xmax = fmaxf(xmax, fabsf(hi));
+                }
             }
             // non-negative floats order like their bit patterns; NaN maps high
             atomicMax(&colmax[c], dmax == dmax ? __float_as_uint(dmax) : 0x7f800000u);
@@ -803,9 +831,20 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                     xs_cols = cap2 >= 16 ? 16 : cap2 >= 8 ? 8 : 4;
                 }
             }
-            for (int i = threadIdx.x >> 5; i < L.n; i += NWARP)
-                for (int c = threadIdx.x & 31; c < L.r; c += 32)
-                    X[(long long)i * L.r + c] = make_float2((float)M[(long long)i * L.LDC + L.n4 + c], 0.0f);
+            {   // X = the FP32 solution; eight loads in flight per thread
+                const int nr = L.n * L.r;
+                for (int e0 = threadIdx.x; e0 < nr; e0 += 8 * NT) {
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int e = e0 + u * NT, i = e / L.r, c = e - i * L.r;
+                        v[u] = e < nr ? (float)M[(long long)i * L.LDC + L.n4 + c] : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (e0 + u * NT < nr) X[e0 + u * NT] = make_float2(v[u], 0.0f);
+                }
+            }
             for (int c = threadIdx.x; c < L.r; c += NT) eta[c] = 1.0f;
             __syncthreads();
             int status = sm.misc[1];
