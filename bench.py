@@ -12,8 +12,12 @@ reported `value`) and plain FP64 (reported beside it).  The metric is leaf
 condensations per second; TFLOP/s use the algorithmic count per leaf
 (2/3 n_i^3 + 2 n_i^2 n_b + 2 n_b^2 (p-2)).
 
-Under torchrun every rank condenses its own copy of the workload (weak
-scaling, no data-path collective); rank 0 prints one JSON line.
+Under torchrun the workload's grid is stacked once per rank in y and split
+into the boxes of its merge tree, one box (the single-GPU workload's 4096
+leaves) per rank: condensation runs with no collective (weak scaling), and
+the reduced solve gathers the box roots' maps on rank 0, merges and solves
+the top levels there and scatters the boxes' boundary values back
+(paper_2211_14969_b300.distributed); rank 0 prints one JSON line.
 `--impl reference` times the FP64 CPU oracle on a bounded sample instead.
 """
 
@@ -474,7 +478,10 @@ def config_block(name, w, ws, graph=False):
                   + 4 * int(p - 2) * w.m for p in w.p) * 8) / 1e9
     return {"workload": f"{name}: {WORKLOADS[name]}",
             "n_leaves_per_rank": w.n_leaves, "p": sorted(set(int(v) for v in w.p)), "m": w.m,
-            "parallelism": f"leaf-parallel, {ws} rank(s), no collective",
+            "parallelism": ("leaf-parallel on 1 GPU" if ws == 1 else
+                            f"{ws} ranks, one merge-tree box of leaves each (the grid stacked {ws}x in y, "
+                            "weak scaling); condensation needs no collective, the reduced solve gathers the "
+                            "box roots on rank 0 and scatters their boundary values (NCCL)"),
             "launch": "CUDA graph replay of the persistent kernel" if graph else "one persistent kernel launch",
             "l2": f"no flush: per step the outputs alone are {out_gb:.2f} GB > 126 MB L2"}
 
@@ -675,12 +682,65 @@ def workload_block(name, ws, pool, steps=3, warmup=3, cpu_seconds=10.0):
     return block
 
 
+def rank_view(w, ws, rank):
+    """Weak scaling over ws ranks: the workload's nx x ny leaf grid stacked
+    ws times in y (nx x ny*ws leaves of the same size on [0,1] x [0,ws],
+    the fields evaluated there), partitioned into the boxes of its merge
+    tree; rank r owns box r, the nx x ny leaves with y in [r, r+1] (rank
+    0's box is the single-GPU workload itself).  Returns the rank's leaves
+    as a workload (local order) and the partition."""
+    from paper_2211_14969_b300 import distributed as D
+    from paper_2211_14969_b300 import workloads as WL
+    part = D.Partition(w.nx, w.ny * ws, ws)
+    if (part.wx0, part.wy0) != (w.nx, w.ny):
+        raise SystemExit("multi-rank runs need a workload grid with nx <= ny")
+    lv = part.leaves(rank)
+    hx, hy = 1.0 / w.nx, 1.0 / w.ny
+    ix, iy = lv // (w.ny * ws), lv % (w.ny * ws)
+    boxes = np.stack([ix * hx, iy * hy, np.full(len(lv), hx), np.full(len(lv), hy)], axis=1)
+    v = WL.scaled(w, w.nx, w.ny)
+    v.p = np.full(len(lv), int(w.p[0]), dtype=np.int32)
+    v.boxes = lambda b=boxes: b
+    return v, part
+
+
+def split_reduced_solve(w, part, plan, out, rank, ws, steps, warmup):
+    """The merge tree split over the ranks (paper_2211_14969_b300.distributed):
+    each rank merges its box to the box root and forms the root's [T | h];
+    rank 0 gathers them over NCCL, merges the grid of boxes and solves it
+    for the boxes' boundary values from outer Dirichlet data; those are
+    scattered back and every rank solves its box.  FP64 leaf maps."""
+    import torch
+    from paper_2211_14969_b300 import distributed as D
+    m = w.m
+    q = int(w.p[0]) - 2
+    be = D.LibraryBackend(int(w.p[0]), w.kappa, part, rank, w.boxes(), plan=plan, out=out)
+    exch = D.TorchExchange(rank, ws, device="cuda")
+    g = torch.from_numpy(np.random.default_rng(7).standard_normal((part.root_nodes(q), m))).cuda()
+    sol = {}
+
+    def step():
+        D.split_merge(be, exch, part, rank, q, m)
+        sol["u"] = D.split_solve(be, exch, part, rank, q, g if rank == 0 else None, m)
+
+    stream = torch.cuda.current_stream()
+    ms = time_steps(step, steps, warmup, ws, stream)
+    nb = part.box_nodes(q)
+    return {"ms": ms / steps, "world": ws, "box_leaves": [part.wx0, part.wy0], "box_grid": [part.bx, part.by],
+            "exchange": f"gather of {ws} root [T | h] blocks ({nb} x {nb + m} FP64 each) on rank 0, scatter of "
+                        f"{ws} boundary blocks ({nb} x {m})",
+            "exchange_bytes": int(ws * nb * (nb + 2 * m) * 8)}
+
+
 def run_gpu(args, rank, ws):
     import torch
     from paper_2211_14969_b300 import hps
     from paper_2211_14969_b300 import workloads as WL
 
     w = make_workload(args.workload)
+    part = None
+    if ws > 1:
+        w, part = rank_view(w, ws, rank)
     if args.leaves:
         full_boxes = w.boxes()[: args.leaves]
         w = WL.scaled(w, w.nx, w.ny)
@@ -753,7 +813,10 @@ def run_gpu(args, rank, ws):
     # merge level (hps_merge) and the downward pass with leaf recovery
     # (hps_solve) for random Dirichlet data
     reduced = None
-    if (len(set(int(v) for v in w.p)) == 1 and "fp64" in outs
+    if part is not None and "fp64" in outs:
+        reduced = {"split_over_ranks": split_reduced_solve(w, part, plan, outs["fp64"], rank, ws,
+                                                           max(3, args.steps // 3), 3)}
+    elif (len(set(int(v) for v in w.p)) == 1 and "fp64" in outs
             and w.nx * w.ny == n and (w.nx & (w.nx - 1)) == 0 and (w.ny & (w.ny - 1)) == 0):
         o = outs["fp64"]
         q = int(w.p[0]) - 2

@@ -174,6 +174,34 @@ hps_status hps_condense_host(hps_plan *plan, hps_prec prec, const double *h_coef
 hps_status hps_merge(hps_plan *plan, int nx, int ny, const double *d_T, const double *d_h, int m,
                      hps_stream stream);
 
+/* hps_merge over a grid of unit BOXES instead of leaves: an nx x ny grid
+ * (box b = bx*ny + by) of boxes of wx0 x wy0 leaves each, tiling an
+ * (nx wx0) x (ny wy0) leaf grid, with DtN maps and fluxes already formed for
+ * every box (d_T packed [nx*ny][nbc0][nbc0], d_h [nx*ny][nbc0][m], nbc0 =
+ * 2 (wx0 + wy0)(p - 2), boundary order [W, E, S, N] as for merged boxes).
+ * The merges are the levels of the whole grid's merge tree above the boxes
+ * (the same schedule as hps_merge, so a box must be a box of that tree:
+ * one the schedule reaches from the leaves).  wx0 = wy0 = 1 is hps_merge
+ * on condensed leaves.  With d_root_Th != NULL the root's own map is formed
+ * there as [T | h], row-major n_root x (n_root + m), n_root = 2 (nx wx0 +
+ * ny wy0)(p - 2) (hps_merge stops before it).  This is what distributing
+ * the merge tree needs (Section 2 merges, one subtree per GPU): each rank
+ * merges its own subtree of leaves up to the subtree's root box and
+ * forms the root's map; one rank merges the grid of those root boxes.
+ * The plan provides p (uniform) and workspace; its n_leaves must equal
+ * nx*ny (for boxes, one plan "leaf" per box: hps_build_leaves with the
+ * boxes' geometry).  Errors as hps_merge. */
+hps_status hps_merge_boxes(hps_plan *plan, int nx, int ny, int wx0, int wy0, const double *d_T, const double *d_h,
+                           int m, double *d_root_Th, hps_stream stream);
+
+/* Top-down pass after hps_merge_boxes: from the Dirichlet data d_g on the
+ * root's boundary (n_root x m, order [W, E, S, N]) to the boundary values
+ * of every unit box, d_ub [nx*ny][nbc0][m] in each box's [W, E, S, N]
+ * order (u3 = S3 [u1; u2] + w3 level by level, Section 2 Remark), which
+ * hps_solve of a box's own leaf plan then takes as its d_g.  m >= 1 and
+ * equal to the merge's m.  HPS_ERR_STATE before a merge. */
+hps_status hps_solve_boxes(hps_plan *plan, const double *d_g, int m, double *d_ub, hps_stream stream);
+
 /* How hps_merge solves Z [S3 | w3] = -[Ta31 Tb32 | ha3 + hb3] (the merge
  * of Section 2 above) on each level.  A level with fewer than `below`
  * merges runs a blocked LU with partial pivoting whose every step is spread
@@ -190,7 +218,8 @@ hps_status hps_set_merge_split(hps_plan *plan, int below);
  * u3 = S3 [u1; u2] + w3, leaf interiors from u_i = S u_b + W.
  * d_u per leaf [p*p][m]: the solution at every node; the four corners are
  * written as 0.  d_S and d_W as written by hps_condense (d_W may be NULL
- * when the merge had m body loads of zero). */
+ * when the merge had m body loads of zero).  HPS_ERR_STATE when the last
+ * merge was an hps_merge_boxes over boxes larger than one leaf. */
 hps_status hps_solve(hps_plan *plan, const double *d_g, const double *d_S, const double *d_W,
                      int m, double *d_u, hps_stream stream);
 
@@ -291,7 +320,7 @@ const char *hps_last_error(const hps_plan *plan);
 /* Free the plan and its workspace (synchronises the device first). */
 void hps_destroy(hps_plan *plan);
 
-/* ABI version: major * 100 + minor. */
+/* ABI version: major * 100 + minor (1.01: hps_merge_boxes, hps_solve_boxes). */
 int hps_version(void);
 
 #ifdef __cplusplus

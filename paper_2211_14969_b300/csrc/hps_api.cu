@@ -131,6 +131,7 @@ struct hps_plan {
     std::vector<Level> levels;
     DevBuf u_leaf;
     int merge_nx = 0, merge_ny = 0, merge_m = -1;
+    int merge_wx0 = 1, merge_wy0 = 1;   // unit box of the last merge (1 x 1: the leaves)
     bool merged = false;
     int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
     SplitAux split_aux{nullptr, nullptr, nullptr};   // look-ahead stream and events, made on first use
@@ -176,7 +177,7 @@ struct hps_plan {
 
 extern "C" {
 
-int hps_version(void) { return 100; }
+int hps_version(void) { return 101; }
 
 const char *hps_last_error(const hps_plan *plan) {
     if (plan == nullptr) return g_build_error.c_str();
@@ -728,14 +729,17 @@ bool pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
 
 }  // namespace
 
-hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const double *d_h, int m,
-                     hps_stream stream) {
+// The merge tree over an nx x ny grid of unit boxes of wx0 x wy0 leaves
+// each (1 x 1: the leaves of hps_condense), whose DtN maps and fluxes are
+// d_T, d_h; with d_root_Th the root's own [T | h] is formed there too.
+static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int wx0, int wy0, const double *d_T,
+                             const double *d_h, int m, double *d_root_Th, hps_stream stream) {
     if (P == nullptr) return HPS_ERR_ARG;
-    if (!P->uniform) return P->fail(HPS_ERR_ARG, "hps_merge: needs one p on every leaf");
-    if (!pow2(nx) || !pow2(ny) || (long long)nx * ny != P->n_leaves)
-        return P->fail(HPS_ERR_ARG, "hps_merge: nx, ny must be powers of two with nx*ny = n_leaves");
+    if (!P->uniform) return P->fail(HPS_ERR_ARG, std::string(who) + ": needs one p on every leaf");
+    if (!pow2(nx) || !pow2(ny) || !pow2(wx0) || !pow2(wy0) || (long long)nx * ny != P->n_leaves)
+        return P->fail(HPS_ERR_ARG, std::string(who) + ": nx, ny, wx0, wy0 must be powers of two with nx*ny = n_leaves");
     if (d_T == nullptr || m < 0 || (m > 0 && d_h == nullptr))
-        return P->fail(HPS_ERR_ARG, "hps_merge: d_T required, d_h required when m > 0");
+        return P->fail(HPS_ERR_ARG, std::string(who) + ": d_T required, d_h required when m > 0");
     const int q = P->pmin - 2;
     cudaStream_t s = (cudaStream_t)stream;
     for (auto &L : P->levels) {
@@ -745,17 +749,27 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
     P->levels.clear();
     P->merged = false;
     const int split_below = P->split_below < 0 ? P->sms : P->split_below;
-    int wx = 1, wy = 1;
+    const int NX = nx * wx0, NY = ny * wy0;   // the whole grid, in leaves
+    int wx = wx0, wy = wy0;
     std::vector<HostLevel> hl;
-    while (wx < nx || wy < ny) {
-        const int dir = (wx < nx && (wx <= wy || wy == ny)) ? 0 : 1;
+    while (wx < NX || wy < NY) {
+        const int dir = (wx < NX && (wx <= wy || wy == NY)) ? 0 : 1;
         HostLevel H;
-        build_level(q, dir, wx, wy, nx / wx, ny / wy, H);
+        build_level(q, dir, wx, wy, NX / wx, NY / wy, H);
         hl.push_back(H);
         if (dir == 0) wx *= 2; else wy *= 2;
     }
     P->levels.resize(hl.size());
     cudaError_t e = cudaSuccess;
+    const int nbc0 = 2 * (wx0 + wy0) * q;   // boundary nodes of a unit box
+    if (hl.empty() && d_root_Th) {
+        // one unit box: the root is the box itself
+        e = cudaMemcpy2DAsync(d_root_Th, (size_t)(nbc0 + m) * sizeof(double), d_T, (size_t)nbc0 * sizeof(double),
+                              (size_t)nbc0 * sizeof(double), nbc0, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && m > 0)
+            e = cudaMemcpy2DAsync(d_root_Th + nbc0, (size_t)(nbc0 + m) * sizeof(double), d_h, (size_t)m * sizeof(double),
+                                  (size_t)m * sizeof(double), nbc0, cudaMemcpyDeviceToDevice, s);
+    }
     for (size_t li = 0; li < hl.size(); ++li) {
         const HostLevel &H = hl[li];
         Level &L = P->levels[li];
@@ -764,6 +778,7 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         const size_t oca = put(H.ca), ocb = put(H.cb), opc = put(H.par_child), opi = put(H.par_idx);
         const size_t o3a = put(H.s3a), o3b = put(H.s3b), osa = put(H.srca), osb = put(H.srcb);
         const bool root = li + 1 == hl.size();
+        const bool form = !root || d_root_Th != nullptr;
         const int lda = (int)round_up(round_up(H.n3, 4) + H.np + m, 4);
         if ((e = L.maps.ensure(maps.size() * sizeof(int))) != cudaSuccess) break;
         if ((e = L.aug.ensure((size_t)H.nm * H.n3 * lda * sizeof(double))) != cudaSuccess) break;
@@ -784,7 +799,7 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
         D.leaf_h = li == 0 ? (m > 0 ? d_h : nullptr) : nullptr;
         D.prev_Th = li == 0 ? nullptr : (const double *)P->levels[li - 1].th.p;
         D.aug = (double *)L.aug.p;
-        D.Th = root ? nullptr : (double *)L.th.p;
+        D.Th = root ? d_root_Th : (double *)L.th.p;
         D.info = (int *)L.info.p;
         D.ipiv = split ? (int *)L.piv.p : nullptr;
         D.u3 = (double *)L.u3.p;
@@ -793,13 +808,15 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
             if ((e = cudaEventCreateWithFlags(&P->split_aux.a, cudaEventDisableTiming)) != cudaSuccess) break;
             if ((e = cudaEventCreateWithFlags(&P->split_aux.b, cudaEventDisableTiming)) != cudaSuccess) break;
         }
-        if ((e = launch_merge_level(D, !root, s, split ? &P->split_aux : nullptr)) != cudaSuccess) break;
+        if ((e = launch_merge_level(D, form, s, split ? &P->split_aux : nullptr)) != cudaSuccess) break;
     }
-    if (e != cudaSuccess) return P->cuda_fail(e, "hps_merge");
-    if ((e = P->u_leaf.ensure((size_t)P->n_leaves * 4 * q * std::max(m, 1) * sizeof(double))) != cudaSuccess)
-        return P->cuda_fail(e, "hps_merge: leaf boundary buffer");
+    if (e != cudaSuccess) return P->cuda_fail(e, who);
+    if ((e = P->u_leaf.ensure((size_t)P->n_leaves * nbc0 * std::max(m, 1) * sizeof(double))) != cudaSuccess)
+        return P->cuda_fail(e, "merge: unit-box boundary buffer");
     P->merge_nx = nx;
     P->merge_ny = ny;
+    P->merge_wx0 = wx0;
+    P->merge_wy0 = wy0;
     P->merge_m = m;
     P->merged = true;
     P->launches = 0;
@@ -810,39 +827,72 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
     return HPS_OK;
 }
 
+hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const double *d_h, int m,
+                     hps_stream stream) {
+    return merge_tree(P, "hps_merge", nx, ny, 1, 1, d_T, d_h, m, nullptr, stream);
+}
+
+hps_status hps_merge_boxes(hps_plan *P, int nx, int ny, int wx0, int wy0, const double *d_T, const double *d_h, int m,
+                           double *d_root_Th, hps_stream stream) {
+    return merge_tree(P, "hps_merge_boxes", nx, ny, wx0, wy0, d_T, d_h, m, d_root_Th, stream);
+}
+
 hps_status hps_set_merge_split(hps_plan *P, int below) {
     if (P == nullptr || below < -1) return HPS_ERR_ARG;
     P->split_below = below;
     return HPS_OK;
 }
 
-hps_status hps_solve(hps_plan *P, const double *d_g, const double *d_S, const double *d_W, int m,
-                     double *d_u, hps_stream stream) {
-    if (P == nullptr) return HPS_ERR_ARG;
-    if (!P->merged) return P->fail(HPS_ERR_STATE, "hps_solve: call hps_merge first");
+// Top-down pass of the last merge: the unit boxes' boundary values into
+// ub (the plan's buffer when null), n_leaves x nbc0 x m.
+static hps_status solve_down(hps_plan *P, const char *who, const double *d_g, int m, double *ub, hps_stream stream,
+                             const double **ub_out) {
+    if (!P->merged) return P->fail(HPS_ERR_STATE, std::string(who) + ": call hps_merge first");
     if (m < 1 || m != P->merge_m)
-        return P->fail(HPS_ERR_ARG, "hps_solve: m must equal the m of hps_merge and be >= 1");
-    if (d_g == nullptr || d_S == nullptr || d_u == nullptr)
-        return P->fail(HPS_ERR_ARG, "hps_solve: d_g, d_S and d_u are required");
+        return P->fail(HPS_ERR_ARG, std::string(who) + ": m must equal the m of the merge and be >= 1");
+    if (d_g == nullptr) return P->fail(HPS_ERR_ARG, std::string(who) + ": d_g is required");
     cudaStream_t s = (cudaStream_t)stream;
-    const int p = P->pmin;
     cudaError_t e = cudaSuccess;
-    const double *ub = d_g;
     const int nl = (int)P->levels.size();
-    for (int li = nl - 1; li >= 0; --li) {
+    double *dst = ub ? ub : (double *)P->u_leaf.p;
+    if (nl == 0) {
+        const int q = P->pmin - 2, nbc0 = 2 * (P->merge_wx0 + P->merge_wy0) * q;
+        e = cudaMemcpyAsync(dst, d_g, (size_t)nbc0 * m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
+    for (int li = nl - 1; li >= 0 && e == cudaSuccess; --li) {
         const Level &L = P->levels[li];
         // parents of level li are the children of level li + 1, whose values
         // the previous iteration wrote into L.u; the root takes the data g
         const double *upar = (li == nl - 1) ? d_g : (const double *)L.u.p;
-        double *uch = li > 0 ? (double *)P->levels[li - 1].u.p : (double *)P->u_leaf.p;
-        if ((e = launch_merge_down(L.dev, upar, uch, s)) != cudaSuccess) break;
-        ub = uch;
+        double *uch = li > 0 ? (double *)P->levels[li - 1].u.p : dst;
+        e = launch_merge_down(L.dev, upar, uch, s);
     }
-    if (e != cudaSuccess) return P->cuda_fail(e, "hps_solve: downward pass");
-    e = launch_leaf_recover(P->n_leaves, p, m, d_S, d_W, ub, d_u, s);
-    if (e != cudaSuccess) return P->cuda_fail(e, "hps_solve: leaf recovery");
-    P->launches = 2 * nl + 1;
+    if (e != cudaSuccess) return P->cuda_fail(e, who);
+    *ub_out = dst;
+    P->launches = 2 * nl;
     return HPS_OK;
+}
+
+hps_status hps_solve(hps_plan *P, const double *d_g, const double *d_S, const double *d_W, int m,
+                     double *d_u, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (P->merged && (P->merge_wx0 != 1 || P->merge_wy0 != 1))
+        return P->fail(HPS_ERR_STATE, "hps_solve: the last merge was over boxes (use hps_solve_boxes)");
+    if (d_S == nullptr || d_u == nullptr) return P->fail(HPS_ERR_ARG, "hps_solve: d_g, d_S and d_u are required");
+    const double *ub = nullptr;
+    const hps_status st = solve_down(P, "hps_solve", d_g, m, nullptr, stream, &ub);
+    if (st != HPS_OK) return st;
+    const cudaError_t e = launch_leaf_recover(P->n_leaves, P->pmin, m, d_S, d_W, ub, d_u, (cudaStream_t)stream);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_solve: leaf recovery");
+    P->launches += 1;
+    return HPS_OK;
+}
+
+hps_status hps_solve_boxes(hps_plan *P, const double *d_g, int m, double *d_ub, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (d_ub == nullptr) return P->fail(HPS_ERR_ARG, "hps_solve_boxes: d_ub is required");
+    const double *ub = nullptr;
+    return solve_down(P, "hps_solve_boxes", d_g, m, d_ub, stream, &ub);
 }
 
 void hps_destroy(hps_plan *P) {

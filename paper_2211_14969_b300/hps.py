@@ -54,6 +54,8 @@ def load_library():
     L.hps_condense_host.argtypes = [vp, i, vp, vp, i, d, i, vp, vp, vp, vp, vp, i, vp]
     L.hps_merge.argtypes = [vp, i, i, vp, vp, i, vp]
     L.hps_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    L.hps_merge_boxes.argtypes = [vp, i, i, i, i, vp, vp, i, vp, vp]
+    L.hps_solve_boxes.argtypes = [vp, vp, i, vp, vp]
     L.hps_leaf_resolve.argtypes = [vp, i, vp, vp, i, vp, d, i, vp, vp, vp]
     L.hps_leaf_recover.argtypes = [vp, vp, vp, i, vp, vp, vp]
     L.hps_set_timing.argtypes = [vp, i]
@@ -69,6 +71,7 @@ def load_library():
     L.hps_destroy.restype = None
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_condense_host", "hps_merge", "hps_solve",
+                 "hps_merge_boxes", "hps_solve_boxes",
                  "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split",
                  "hps_fallback_count",
                  "hps_phase_times", "hps_last_launch_count"):
@@ -161,6 +164,12 @@ class Plan:
 
     def solve(self, g, S, W, m, out=None, stream=None):
         return hps_solve(self, g, S, W, m, out, stream)
+
+    def merge_boxes(self, nx, ny, wx0, wy0, T, h, m, root=False, stream=None):
+        return hps_merge_boxes(self, nx, ny, wx0, wy0, T, h, m, root, stream)
+
+    def solve_boxes(self, g, m, out=None, stream=None):
+        return hps_solve_boxes(self, g, m, out, stream)
 
     def leaf_resolve(self, coef, ub, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, out=None, stream=None):
         return hps_leaf_resolve(self, coef, ub, f, m, prec, tol, kmax, out, stream)
@@ -312,6 +321,45 @@ def hps_merge(plan, nx, ny, T, h, m, stream=None):
     _check_dev(T, "T", int(plan.layout.o_bb[-1]))
     status = load_library().hps_merge(plan.handle, int(nx), int(ny), _ptr(T), _ptr(h), int(m), _stream(stream))
     plan.check(status, "hps_merge")
+    plan._unit_box = (1, 1)
+
+
+def _box_nodes(plan, wx0, wy0):
+    q = int(plan.layout.p[0]) - 2
+    return 2 * (wx0 + wy0) * q
+
+
+def hps_merge_boxes(plan, nx, ny, wx0, wy0, T, h, m, root=False, stream=None):
+    """Merge an nx x ny grid of unit boxes of wx0 x wy0 leaves whose maps T
+    ([nx*ny][nbc0][nbc0]) and fluxes h ([nx*ny][nbc0][m]) are given; with
+    root=True returns the root's [T | h] (n_root x (n_root + m))."""
+    import torch
+    nbc0 = _box_nodes(plan, wx0, wy0)
+    _check_dev(T, "T", nx * ny * nbc0 * nbc0)
+    _check_dev(h, "h", nx * ny * nbc0 * m if m > 0 else None)
+    th = None
+    if root:
+        nr = _box_nodes(plan, nx * wx0, ny * wy0)
+        th = torch.empty(nr * (nr + m), dtype=torch.float64, device=T.device)
+    status = load_library().hps_merge_boxes(plan.handle, int(nx), int(ny), int(wx0), int(wy0), _ptr(T), _ptr(h),
+                                            int(m), _ptr(th), _stream(stream))
+    plan.check(status, "hps_merge_boxes")
+    plan._unit_box = (int(wx0), int(wy0))
+    return th
+
+
+def hps_solve_boxes(plan, g, m, out=None, stream=None):
+    """Boundary values of every unit box of the last hps_merge_boxes from the
+    root's Dirichlet data g: [n_boxes][nbc0][m]."""
+    import torch
+    _check_dev(g, "g")
+    wx0, wy0 = getattr(plan, "_unit_box", (1, 1))
+    n = plan.layout.n_leaves * _box_nodes(plan, wx0, wy0) * m
+    ub = out if out is not None else torch.empty(n, dtype=torch.float64, device=g.device)
+    _check_dev(ub, "ub", n)
+    status = load_library().hps_solve_boxes(plan.handle, _ptr(g), int(m), _ptr(ub), _stream(stream))
+    plan.check(status, "hps_solve_boxes")
+    return ub
 
 
 def hps_leaf_resolve(plan, coef, ub, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, out=None, stream=None):
