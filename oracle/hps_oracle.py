@@ -427,6 +427,163 @@ def key_coords(p, key, nx, ny, lx=1.0, ly=1.0, x0=0.0, y0=0.0):
 
 
 # ----------------------------------------------------------------------------
+# SlabLU: the reduced system of Eq. (hps_reduced) in the slab block form of
+# Eq. (dell1); slab interiors eliminated, the block-tridiagonal interface
+# system factored densely (Section 2, the SlabLU paragraphs)
+# ----------------------------------------------------------------------------
+
+
+def reduced_system(p, nx, ny, leaves, g_keys):
+    """The reduced system A~ u~ = f~ of Eq. (hps_reduced): the unknowns are
+    the leaf edge nodes not on the outer boundary; each has one row, the
+    flux continuity there (the outward fluxes T u_b + h of the two leaves
+    sharing the node sum to zero).  Outer edge nodes carry the Dirichlet
+    data g_keys and move to the right-hand side.  leaves[ix * ny + iy] holds
+    the leaf's T and h.  Returns (A, f, keys): keys[i] names unknown i."""
+    outer = set(outer_boundary_keys(p, nx, ny))
+    keys, kid = [], {}
+    for ix in range(nx):
+        for iy in range(ny):
+            for k in box_keys(p, ix, iy, 1, 1):
+                if k not in outer and k not in kid:
+                    kid[k] = len(keys)
+                    keys.append(k)
+    m = np.asarray(leaves[0]["h"]).reshape(4 * (p - 2), -1).shape[1]
+    n = len(keys)
+    A = np.zeros((n, n))
+    f = np.zeros((n, m))
+    for ix in range(nx):
+        for iy in range(ny):
+            lf = leaves[ix * ny + iy]
+            T = lf["T"]
+            h = np.asarray(lf["h"]).reshape(T.shape[0], m)
+            lk = box_keys(p, ix, iy, 1, 1)
+            for r, k in enumerate(lk):
+                if k in outer:
+                    continue
+                row = kid[k]
+                f[row] -= h[r]
+                for c, kc in enumerate(lk):
+                    if kc in outer:
+                        f[row] -= T[r, c] * np.atleast_1d(g_keys[kc])
+                    else:
+                        A[row, kid[kc]] += T[r, c]
+    return A, f, keys
+
+
+def slab_blocks(p, nx, s, keys):
+    """Eq. (dell1)'s blocks for slabs of s leaf columns (vertical strips,
+    x from 0): interface k = 1..S-1 is the vertical grid line x = k s hx,
+    every other unknown is interior to the slab that contains it (a vertical
+    line x = l hx inside slab l // s, or a horizontal edge of leaf column ix
+    in slab ix // s).  Returns (interior index lists I[0..S-1], interface
+    index lists G[1..S-1] as G[0..S-2])."""
+    if nx % s or s < 2:
+        raise ValueError("slab width must divide nx and be at least 2 leaves")
+    S = nx // s
+    I = [[] for _ in range(S)]
+    G = [[] for _ in range(S - 1)]
+    for i, (kind, line, seg, _) in enumerate(keys):
+        if kind == "v" and line % s == 0:
+            G[line // s - 1].append(i)
+        elif kind == "v":
+            I[line // s].append(i)
+        else:
+            I[seg // s].append(i)
+    return I, G
+
+
+def slab_solve(p, nx, ny, s, leaves, g_keys):
+    """SlabLU on the reduced system (Section 2, Eq. (dell1)): order the
+    unknowns as slab interiors and the interfaces between slabs; eliminate
+    each slab's interior (dense solves with its diagonal block); the
+    Schur complement on the interfaces is block tridiagonal, and is solved
+    by block LU (forward elimination over the interfaces, then back
+    substitution); the slab interiors follow from the interface values.
+    Returns the values of all unknowns by key."""
+    A, f, keys = reduced_system(p, nx, ny, leaves, g_keys)
+    I, G = slab_blocks(p, nx, s, keys)
+    S = len(I)
+    ix = np.ix_
+    # slab interiors: A_II^{-1} applied to [A_I,Gleft  A_I,Gright  f_I]
+    elim = []
+    for j in range(S):
+        left = G[j - 1] if j > 0 else []
+        right = G[j] if j < S - 1 else []
+        Aii = A[ix(I[j], I[j])]
+        X = np.linalg.solve(Aii, np.hstack([A[ix(I[j], left)], A[ix(I[j], right)], f[I[j]]]))
+        elim.append((left, right, X))
+    # block tridiagonal interface system: D_k u_k + L_k u_{k-1} + U_k u_{k+1} = r_k
+    D, L, U, r = [], [], [], []
+    for k in range(S - 1):
+        g = G[k]
+        Dk = A[ix(g, g)].copy()
+        rk = f[g].copy()
+        Lk = Uk = None
+        for j in (k, k + 1):            # the slabs left and right of interface k
+            left, right, X = elim[j]
+            AgI = A[ix(g, I[j])]
+            nl, nr = len(left), len(right)
+            XL, XR, Xf = X[:, :nl], X[:, nl:nl + nr], X[:, nl + nr:]
+            rk -= AgI @ Xf
+            if j == k:                  # slab k: interface k is its right side
+                Dk -= AgI @ XR
+                if nl:
+                    Lk = A[ix(g, left)] - AgI @ XL
+            else:                       # slab k + 1: interface k is its left side
+                Dk -= AgI @ XL
+                if nr:
+                    Uk = A[ix(g, right)] - AgI @ XR
+        D.append(Dk)
+        L.append(Lk)
+        U.append(Uk)
+        r.append(rk)
+    # block LU: Delta_k = D_k - L_k Delta_{k-1}^{-1} U_{k-1}, then back substitution
+    Delta, y = [], []
+    for k in range(S - 1):
+        if k == 0:
+            Delta.append(D[0])
+            y.append(r[0])
+        else:
+            Z = np.linalg.solve(Delta[k - 1], np.hstack([U[k - 1], y[k - 1]]))
+            nu = U[k - 1].shape[1]
+            Delta.append(D[k] - L[k] @ Z[:, :nu])
+            y.append(r[k] - L[k] @ Z[:, nu:])
+    u = [None] * (S - 1)
+    for k in reversed(range(S - 1)):
+        rhs = y[k] if k == S - 2 else y[k] - U[k] @ u[k + 1]
+        u[k] = np.linalg.solve(Delta[k], rhs)
+    vals = {}
+    for k in range(S - 1):
+        for i, v in zip(G[k], u[k]):
+            vals[keys[i]] = v
+    for j in range(S):
+        left, right, X = elim[j]
+        sides = ([u[j - 1]] if j > 0 else []) + ([u[j]] if j < S - 1 else [])
+        ub = np.vstack([np.zeros((0, f.shape[1]))] + sides)
+        nl, nr = len(left), len(right)
+        ui = X[:, nl + nr:] - X[:, :nl + nr] @ ub
+        for i, v in zip(I[j], ui):
+            vals[keys[i]] = v
+    return vals
+
+
+def slab_downward(p, nx, ny, s, leaves, g_keys):
+    """slab_solve, then every leaf's edge values from the reduced solution
+    and the Dirichlet data, and its interior values u_i = S u_b + W: per
+    leaf (u_b, u_i) in the form hps_downward returns."""
+    vals = dict(g_keys)
+    vals.update(slab_solve(p, nx, ny, s, leaves, g_keys))
+    out = []
+    for ix in range(nx):
+        for iy in range(ny):
+            lf = leaves[ix * ny + iy]
+            ub = np.array([np.atleast_1d(vals[k]) for k in box_keys(p, ix, iy, 1, 1)])
+            out.append({"u_b": ub, "u_i": lf["S"] @ ub + lf["W"]})
+    return out
+
+
+# ----------------------------------------------------------------------------
 # Brute-force global collocation system (Eq. (Au=f)), independent of merges
 # ----------------------------------------------------------------------------
 

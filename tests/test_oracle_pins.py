@@ -478,3 +478,113 @@ def test_planted_mistake_is_caught(monkeypatch, mutation):
         return
     leaf, grid = _leaf_pins()
     assert max(leaf, grid) > 1e-6, (leaf, grid)
+
+
+# ------------------------------------------------------------------ SlabLU
+
+def _grid_leaves(p, nx, ny, coefs, kappa, fs):
+    boxes = O.grid_boxes(nx, ny)
+    return [O.condense_leaf(p, boxes[l], coefs[l], kappa, fs[l]) for l in range(nx * ny)]
+
+
+def _gkeys(p, nx, ny, g_fn):
+    return {k: np.atleast_1d(g_fn(*O.key_coords(p, k, nx, ny))) for k in O.outer_boundary_keys(p, nx, ny)}
+
+
+def test_reduced_system_holds_for_the_merge_tree_solution():
+    """The merge tree's edge values satisfy every flux-continuity row of the
+    reduced system of Eq. (hps_reduced) to rounding; its size is the number
+    of interface nodes (896 for 8 x 8 leaves of p = 10)."""
+    p = 10
+    w, coefs, fs = planewave_case(p)
+    sol, leaves = hps_grid_solve(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+    A, f, keys = O.reduced_system(p, 8, 8, leaves, _gkeys(p, 8, 8, w.dirichlet_data))
+    assert A.shape == (896, 896)
+    vals = {}
+    for l, s in enumerate(sol):
+        ix, iy = divmod(l, 8)
+        for k, v in zip(O.box_keys(p, ix, iy, 1, 1), s["u_b"]):
+            vals[k] = v
+    u = np.array([vals[k] for k in keys])
+    assert np.abs(A @ u - f).max() / (np.abs(A) @ np.abs(u) + np.abs(f)).max() < 1e-13
+
+
+@pytest.mark.parametrize("s", [2, 4])
+def test_slab_blocks_are_block_tridiagonal(s):
+    """Eq. (dell1): slab interiors do not interact with each other, a slab
+    touches only the interfaces on its two sides, an interface only the
+    slabs beside it (slabs at least two leaves wide)."""
+    p, nx, ny = 6, 8, 4
+    rng = np.random.default_rng(2)
+    coefs = [random_coef(rng, p * p) for _ in range(nx * ny)]
+    fs = [rng.standard_normal((p * p, 1)) for _ in range(nx * ny)]
+    leaves = _grid_leaves(p, nx, ny, coefs, 5.0, fs)
+    A, _, keys = O.reduced_system(p, nx, ny, leaves, _gkeys(p, nx, ny, lambda x, y: 0.0 * x))
+    I, G = O.slab_blocks(p, nx, s, keys)
+    S = nx // s
+    assert len(I) == S and len(G) == S - 1
+    assert sorted(sum(I, []) + sum(G, [])) == list(range(len(keys)))
+    for a in range(S):
+        for b in range(S):
+            blk = A[np.ix_(I[a], I[b])]
+            assert (np.abs(blk).max() > 0) == (a == b), (a, b)
+        for k in range(S - 1):
+            touches = np.abs(A[np.ix_(I[a], G[k])]).max() > 0
+            assert touches == (k in (a - 1, a)), (a, k)
+    for k in range(S - 1):
+        for k2 in range(S - 1):
+            assert (np.abs(A[np.ix_(G[k], G[k2])]).max() > 0) == (k == k2)
+
+
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_slab_solve_equals_merge_tree_and_dense_solve(s):
+    """SlabLU and the merge tree eliminate the same reduced system in
+    different orders: same solution; and the brute-force dense solve of
+    the global system (plane wave, kappa = 20, p = 10, 8 x 8 leaves)."""
+    p = 10
+    w, coefs, fs = planewave_case(p)
+    sol, leaves = hps_grid_solve(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+    slab = O.slab_downward(p, 8, 8, s, leaves, _gkeys(p, 8, 8, w.dirichlet_data))
+    ref = [(d["u_b"], d["u_i"]) for d in sol]
+    assert grid_error(slab, ref) < 1e-12
+    dense, _ = O.global_dense_solve(p, 8, 8, coefs, w.kappa, fs, w.dirichlet_data)
+    assert grid_error(slab, [(d["u_b"], d["u_i"]) for d in dense]) < 1e-10
+
+
+def test_slab_solve_manufactured():
+    """A tensor polynomial of degree p-1 with random coefficient samples is
+    reproduced exactly through condensation and SlabLU (4 slabs of 2)."""
+    p, nx, ny, kappa = 8, 8, 4, 7.0
+    rng = np.random.default_rng(17)
+    u = random_poly(rng, p - 1, p - 1, xc=0.5, yc=0.5, sx=0.5, sy=0.5)
+    coefs, fs = [], []
+    for box in O.grid_boxes(nx, ny):
+        x, y = O.leaf_nodes(p, box)
+        c = random_coef(rng, p * p)
+        coefs.append(c)
+        fs.append(u.apply_operator(x, y, c, kappa)[:, None])
+    leaves = _grid_leaves(p, nx, ny, coefs, kappa, fs)
+    sol = O.slab_downward(p, nx, ny, 2, leaves, _gkeys(p, nx, ny, lambda x, y: u(x, y)))
+    assert grid_error(sol, nodal_values(p, nx, ny, u)) < 1e-10
+
+
+def test_slab_planted_mistakes_are_caught(monkeypatch):
+    """A horizontal edge put in the neighbouring slab breaks the block form;
+    a sign error in the reduced system's Dirichlet terms breaks the solve."""
+    real = O.slab_blocks
+
+    def shifted(p, nx, s, keys):
+        I, G = real(p, nx, s, keys)
+        moved = [i for i in I[0] if keys[i][0] == "h"][:1]
+        return [[i for i in I[0] if i not in moved]] + [I[1] + moved] + I[2:], G
+    monkeypatch.setattr(O, "slab_blocks", shifted)
+    with pytest.raises(AssertionError):
+        test_slab_blocks_are_block_tridiagonal(2)
+    monkeypatch.setattr(O, "slab_blocks", real)
+    real_rs = O.reduced_system
+
+    def flipped(p, nx, ny, leaves, g_keys):
+        return real_rs(p, nx, ny, leaves, {k: -v for k, v in g_keys.items()})
+    monkeypatch.setattr(O, "reduced_system", flipped)
+    with pytest.raises(AssertionError):
+        test_slab_solve_equals_merge_tree_and_dense_solve(2)
