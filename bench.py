@@ -835,6 +835,11 @@ def run_gpu(args, rank, ws):
                                 "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
                    "gpu_launches_merge": merge_launches, "flux_mismatch": flux_mismatch(w, lay, o, u, m),
                    "clocks": cs.summary()}
+        # SlabLU (Section 2, Eq. (dell1)) on the same leaf maps and data
+        if w.nx >= 16:
+            sl, u_slab = slab_timing(w, plan, o, g, 16, rs, 3, ws)
+            sl["u_relerr_vs_merge_tree"] = float((u_slab - u).norm() / u.norm())
+            reduced["slablu"] = sl
 
     line = None
     if rank == 0:
@@ -964,6 +969,55 @@ def merge_flops(q, nx, ny, m):
     return total, levels
 
 
+def slab_flops(q, nx, ny, s, m):
+    """Algorithmic flops of hps_slab_factor: the merges inside the slabs (per
+    merge as merge_flops, every level forming its parent's [T | h], the
+    slabs' own maps included) and the block LU over the S - 1 interfaces of
+    n = ny q nodes (per interface the LU of Delta (2/3 n^3), the solve for
+    its 2n + m right-hand columns (2 n^2 (2n + m)) and, after the first,
+    Delta_k = D_k + L_k S_{k-1} with its body-load column (2 n^2 (n + m)))."""
+    wx = wy = 1
+    total = 0.0
+    while wx < s or wy < ny:
+        along_x = wx < s and (wx <= wy or wy == ny)
+        n3 = (wy if along_x else wx) * q
+        npar = 2 * ((2 * wx + wy) if along_x else (wx + 2 * wy)) * q
+        if along_x:
+            wx *= 2
+        else:
+            wy *= 2
+        nm = (nx // wx) * (ny // wy)
+        total += nm * (2.0 / 3.0 * n3 ** 3 + 2.0 * n3 ** 2 * (npar + m) + 2.0 * npar * n3 * (npar + m))
+    n = ny * q
+    S = nx // s
+    for k in range(S - 1):
+        total += 2.0 / 3.0 * n ** 3 + 2.0 * n ** 2 * (2 * n + m) + (2.0 * n ** 2 * (n + m) if k else 0.0)
+    return total
+
+
+def slab_timing(w, plan, out, g, s, steps, warmup, ws):
+    """hps_slab_factor and hps_slab_solve (SlabLU, slabs of s leaf columns)
+    on the plan's grid from the FP64 leaf maps, timed like the merge tree;
+    the solution's flux continuity across every interior edge."""
+    import torch
+    stream = torch.cuda.current_stream()
+    m = w.m
+    q = int(w.p[0]) - 2
+    with ClockSampler(gpu_uuid()) as cs:
+        t_f = time_steps(lambda: plan.slab_factor(w.nx, w.ny, s, out["T"], out["h"], m), steps, warmup, ws, stream)
+    launches = plan.last_launch_count()
+    u = torch.empty(int(plan.layout.o_p2[-1]) * m, dtype=torch.float64, device="cuda")
+    t_s = time_steps(lambda: plan.slab_solve(g, out["S"], out["W"], m, out=u), steps, warmup, ws, stream)
+    fl = slab_flops(q, w.nx, w.ny, s, m)
+    tf = fl / (t_f / steps * 1e-3) / 1e12
+    return {"slab_leaf_columns": s, "interfaces": w.nx // s - 1, "interface_nodes": w.ny * q,
+            "factor_ms": t_f / steps, "solve_ms": t_s / steps, "factor_gflop": fl / 1e9, "factor_tflops": tf,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s", "frac": tf / 1.25,
+                         "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
+            "gpu_launches_factor": launches, "flux_mismatch": flux_mismatch(w, plan.layout, out, u, m),
+            "clocks": cs.summary()}, u
+
+
 def flux_mismatch(w, lay, out, u, m):
     """Flux continuity of a solved grid: per leaf the outward flux T u_b + h
     at its edge nodes [W, E, S, N]; across every interior edge the two
@@ -1025,6 +1079,14 @@ def run_merge_solve(args, rank, ws):
         else:
             row["u_relerr_vs_split"] = float((u - u_ref).norm() / u_ref.norm())
         res[name] = row
+    plan.set_merge_split(-1)
+    slabs = {}
+    for sw in (4, 8, 16):
+        if sw <= w.nx:
+            sl, u_slab = slab_timing(w, plan, out, g, sw, args.steps, args.warmup, ws)
+            sl["u_relerr_vs_merge_tree"] = float((u_slab - u_ref).norm() / u_ref.norm())
+            slabs[f"s={sw}"] = sl
+    res["slablu"] = slabs
     if rank == 0:
         pk = 1.25
         sp = res["split"]
@@ -1060,7 +1122,8 @@ def main(argv=None):
                     help="bumps_p20 (default, the headline workload) or another seeded workload")
     ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the launch")
     ap.add_argument("--merge-solve", action="store_true",
-                    help="time hps_merge + hps_solve on the workload's grid (split vs one CTA per merge)")
+                    help="time hps_merge + hps_solve on the workload's grid (split vs one CTA per merge) and "
+                         "SlabLU (hps_slab_factor + hps_slab_solve) for slab widths 4, 8, 16")
     ap.add_argument("--leaf-solve", action="store_true",
                     help="time the leaf solve after the reduced solve: stored S vs re-factored leaves")
     args = ap.parse_args(argv)

@@ -202,6 +202,32 @@ hps_status hps_merge_boxes(hps_plan *plan, int nx, int ny, int wx0, int wy0, con
  * equal to the merge's m.  HPS_ERR_STATE before a merge. */
 hps_status hps_solve_boxes(hps_plan *plan, const double *d_g, int m, double *d_ub, hps_stream stream);
 
+/* SlabLU, the paper's second solver for the reduced system of
+ * Eq. (hps_reduced) (Section 2, the block form of Eq. (dell1)), on a
+ * uniform-p nx x ny grid of condensed leaves (leaf l = ix*ny + iy, nx and
+ * ny powers of two).  The grid is cut into S = nx / s slabs of s leaf
+ * columns (s a power of two, 2 <= s <= nx).  Factor: the nodes interior to
+ * every slab are eliminated (by the merges inside the slab, which leave the
+ * slab's DtN map on its boundary; the Schur complement is the one the
+ * paper's per-slab sparse factorization gives), and the block-tridiagonal
+ * system on the S - 1 interfaces (nodes on the vertical lines between
+ * slabs, ny (p-2) each) is factored by dense block LU in FP64 (one
+ * interface after the other, each step a dense LU over many CTAs).  The
+ * factorization keeps explicit operators, so hps_slab_solve for new
+ * Dirichlet data is matrix-vector products plus the downward pass inside
+ * the slabs and the leaf recovery.  d_T, d_h as written by hps_condense;
+ * m >= 1.  The plan's merge state is replaced (hps_solve then needs a new
+ * hps_merge).  Errors: HPS_ERR_ARG (sizes), HPS_ERR_CUDA / HPS_ERR_OOM. */
+hps_status hps_slab_factor(hps_plan *plan, int nx, int ny, int s, const double *d_T, const double *d_h, int m,
+                           hps_stream stream);
+
+/* The solve after hps_slab_factor: d_g Dirichlet data on the grid's outer
+ * boundary (order [W, E, S, N], n_outer x m, as hps_solve), d_S and d_W as
+ * written by hps_condense; d_u per leaf [p*p][m] as hps_solve.
+ * HPS_ERR_STATE before hps_slab_factor, HPS_ERR_ARG for another m. */
+hps_status hps_slab_solve(hps_plan *plan, const double *d_g, const double *d_S, const double *d_W, int m, double *d_u,
+                          hps_stream stream);
+
 /* How hps_merge solves Z [S3 | w3] = -[Ta31 Tb32 | ha3 + hb3] (the merge
  * of Section 2 above) on each level.  A level with fewer than `below`
  * merges runs a blocked LU with partial pivoting whose every step is spread
@@ -320,7 +346,8 @@ const char *hps_last_error(const hps_plan *plan);
 /* Free the plan and its workspace (synchronises the device first). */
 void hps_destroy(hps_plan *plan);
 
-/* ABI version: major * 100 + minor (1.01: hps_merge_boxes, hps_solve_boxes). */
+/* ABI version: major * 100 + minor (1.01: hps_merge_boxes, hps_solve_boxes;
+ * 1.02: hps_slab_factor, hps_slab_solve). */
 int hps_version(void);
 
 #ifdef __cplusplus

@@ -133,6 +133,10 @@ struct hps_plan {
     int merge_nx = 0, merge_ny = 0, merge_m = -1;
     int merge_wx0 = 1, merge_wy0 = 1;   // unit box of the last merge (1 x 1: the leaves)
     bool merged = false;
+    // SlabLU: the slabs' [T | h], the interfaces' solved systems, solve scratch
+    DevBuf slab_th, slab_aug, slab_piv, slab_info, slab_tmp;
+    int slab_nx = 0, slab_ny = 0, slab_s = 0, slab_m = -1;
+    bool slabbed = false;
     int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
     SplitAux split_aux{nullptr, nullptr, nullptr};   // look-ahead stream and events, made on first use
     // hps_condense_host: device copies of the inputs and outputs, the chunk
@@ -177,7 +181,7 @@ struct hps_plan {
 
 extern "C" {
 
-int hps_version(void) { return 101; }
+int hps_version(void) { return 102; }
 
 const char *hps_last_error(const hps_plan *plan) {
     if (plan == nullptr) return g_build_error.c_str();
@@ -733,7 +737,7 @@ bool pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
 // each (1 x 1: the leaves of hps_condense), whose DtN maps and fluxes are
 // d_T, d_h; with d_root_Th the root's own [T | h] is formed there too.
 static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int wx0, int wy0, const double *d_T,
-                             const double *d_h, int m, double *d_root_Th, hps_stream stream) {
+                             const double *d_h, int m, double *d_root_Th, hps_stream stream, int tx = 0, int ty = 0) {
     if (P == nullptr) return HPS_ERR_ARG;
     if (!P->uniform) return P->fail(HPS_ERR_ARG, std::string(who) + ": needs one p on every leaf");
     if (!pow2(nx) || !pow2(ny) || !pow2(wx0) || !pow2(wy0) || (long long)nx * ny != P->n_leaves)
@@ -748,12 +752,18 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
     }
     P->levels.clear();
     P->merged = false;
+    P->slabbed = false;
     const int split_below = P->split_below < 0 ? P->sms : P->split_below;
     const int NX = nx * wx0, NY = ny * wy0;   // the whole grid, in leaves
+    // merges stop at boxes of tx x ty leaves (default: the whole grid; the
+    // slabs of SlabLU stop at s x NY): x merges while below tx, alternating
+    // with y as in the full tree
+    if (tx <= 0) tx = NX;
+    if (ty <= 0) ty = NY;
     int wx = wx0, wy = wy0;
     std::vector<HostLevel> hl;
-    while (wx < NX || wy < NY) {
-        const int dir = (wx < NX && (wx <= wy || wy == NY)) ? 0 : 1;
+    while (wx < tx || wy < ty) {
+        const int dir = (wx < tx && (wx <= wy || wy == ty)) ? 0 : 1;
         HostLevel H;
         build_level(q, dir, wx, wy, NX / wx, NY / wy, H);
         hl.push_back(H);
@@ -843,6 +853,23 @@ hps_status hps_set_merge_split(hps_plan *P, int below) {
     return HPS_OK;
 }
 
+// The downward pass through the stored levels: from the top level's parent
+// values upar (one block of np x m per merge of that level) to the unit
+// boxes' boundary values in dst.
+static cudaError_t down_levels(hps_plan *P, const double *upar, double *dst, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    const int nl = (int)P->levels.size();
+    for (int li = nl - 1; li >= 0 && e == cudaSuccess; --li) {
+        const Level &L = P->levels[li];
+        // parents of level li are the children of level li + 1, whose values
+        // the previous iteration wrote into L.u; the top level takes upar
+        const double *up = (li == nl - 1) ? upar : (const double *)L.u.p;
+        double *uch = li > 0 ? (double *)P->levels[li - 1].u.p : dst;
+        e = launch_merge_down(L.dev, up, uch, s);
+    }
+    return e;
+}
+
 // Top-down pass of the last merge: the unit boxes' boundary values into
 // ub (the plan's buffer when null), n_leaves x nbc0 x m.
 static hps_status solve_down(hps_plan *P, const char *who, const double *d_g, int m, double *ub, hps_stream stream,
@@ -858,14 +885,8 @@ static hps_status solve_down(hps_plan *P, const char *who, const double *d_g, in
     if (nl == 0) {
         const int q = P->pmin - 2, nbc0 = 2 * (P->merge_wx0 + P->merge_wy0) * q;
         e = cudaMemcpyAsync(dst, d_g, (size_t)nbc0 * m * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    }
-    for (int li = nl - 1; li >= 0 && e == cudaSuccess; --li) {
-        const Level &L = P->levels[li];
-        // parents of level li are the children of level li + 1, whose values
-        // the previous iteration wrote into L.u; the root takes the data g
-        const double *upar = (li == nl - 1) ? d_g : (const double *)L.u.p;
-        double *uch = li > 0 ? (double *)P->levels[li - 1].u.p : dst;
-        e = launch_merge_down(L.dev, upar, uch, s);
+    } else {
+        e = down_levels(P, d_g, dst, s);
     }
     if (e != cudaSuccess) return P->cuda_fail(e, who);
     *ub_out = dst;
@@ -895,6 +916,121 @@ hps_status hps_solve_boxes(hps_plan *P, const double *d_g, int m, double *d_ub, 
     return solve_down(P, "hps_solve_boxes", d_g, m, d_ub, stream, &ub);
 }
 
+// ---------------------------------------------------------------------------
+// SlabLU (slab.cu): slab merges, block LU of the interface system, solve
+// ---------------------------------------------------------------------------
+
+hps_status hps_slab_factor(hps_plan *P, int nx, int ny, int s, const double *d_T, const double *d_h, int m,
+                           hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (!pow2(s) || s < 2 || s > nx)
+        return P->fail(HPS_ERR_ARG, "hps_slab_factor: the slab width s must be a power of two, 2 <= s <= nx");
+    if (m < 1) return P->fail(HPS_ERR_ARG, "hps_slab_factor: m >= 1 body-load columns are required");
+    const int q = P->pmin - 2, n = ny * q, S = nx / s, nps = 2 * (s + ny) * q, ldt = nps + m;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = P->slab_th.ensure((size_t)S * nps * ldt * sizeof(double));
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_slab_factor: slab maps");
+    // the slabs' interiors: merges inside every slab up to its [T | h]
+    hps_status r = merge_tree(P, "hps_slab_factor", nx, ny, 1, 1, d_T, d_h, m, (double *)P->slab_th.p, stream, s, ny);
+    if (r != HPS_OK) return r;
+    P->merged = false;   // the stored levels stop at the slabs: only hps_slab_solve uses them
+    int launches = P->launches;
+    if (S > 1) {
+        const int c3 = (int)round_up(n, 4), lda = (int)round_up(c3 + 2 * n + m, 4);
+        if ((e = P->slab_aug.ensure((size_t)(S - 1) * n * lda * sizeof(double))) != cudaSuccess ||
+            (e = P->slab_piv.ensure((size_t)(S - 1) * n * sizeof(int))) != cudaSuccess ||
+            (e = P->slab_info.ensure((size_t)(S - 1) * sizeof(int))) != cudaSuccess)
+            return P->cuda_fail(e, "hps_slab_factor: interface systems");
+        const bool split = split_solve_fits(n);
+        if (split && P->split_aux.side == nullptr) {
+            if ((e = cudaStreamCreateWithFlags(&P->split_aux.side, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&P->split_aux.a, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&P->split_aux.b, cudaEventDisableTiming)) != cudaSuccess)
+                return P->cuda_fail(e, "hps_slab_factor: streams");
+        }
+        double *aug = (double *)P->slab_aug.p;
+        const double *th = (const double *)P->slab_th.p;
+        for (int k = 0; k < S - 1 && e == cudaSuccess; ++k) {
+            SlabStepDev D{};
+            D.n = n; D.m = m; D.ldt = ldt; D.np = nps; D.lda = lda; D.c3 = c3; D.last = k == S - 2;
+            D.left = th + (size_t)k * nps * ldt;
+            D.right = th + (size_t)(k + 1) * nps * ldt;
+            D.prev = k > 0 ? aug + (size_t)(k - 1) * n * lda : nullptr;
+            D.aug = aug + (size_t)k * n * lda;
+            if ((e = launch_slab_assemble(D, st)) != cudaSuccess) break;
+            MergeLevelDev L{};
+            L.nm = 1; L.n3 = n; L.c3 = c3; L.np = 2 * n; L.nbc = 0; L.m = m; L.lda = lda;
+            L.aug = D.aug;
+            L.info = (int *)P->slab_info.p + k;
+            L.ipiv = (int *)P->slab_piv.p + (size_t)k * n;
+            e = split ? launch_split_solve(L, L.ipiv, st, &P->split_aux)
+                      : launch_dense_solve(D.aug, 0, n, c3, c3 + 2 * n + m, lda, 1, L.info, st);
+            launches += 2 + (split ? 6 * ((n + 15) / 16) - 3 : 1);
+        }
+        if (e != cudaSuccess) return P->cuda_fail(e, "hps_slab_factor: interface block LU");
+    }
+    if ((e = P->slab_tmp.ensure((size_t)(2 * (S + 1) * n + (size_t)S * nps) * m * sizeof(double))) != cudaSuccess)
+        return P->cuda_fail(e, "hps_slab_factor: solve scratch");
+    P->slab_nx = nx; P->slab_ny = ny; P->slab_s = s; P->slab_m = m;
+    P->slabbed = true;
+    P->launches = launches;
+    return HPS_OK;
+}
+
+hps_status hps_slab_solve(hps_plan *P, const double *d_g, const double *d_S, const double *d_W, int m, double *d_u,
+                          hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (!P->slabbed) return P->fail(HPS_ERR_STATE, "hps_slab_solve: call hps_slab_factor first");
+    if (m != P->slab_m) return P->fail(HPS_ERR_ARG, "hps_slab_solve: m must equal the m of hps_slab_factor");
+    if (d_g == nullptr || d_S == nullptr || d_u == nullptr)
+        return P->fail(HPS_ERR_ARG, "hps_slab_solve: d_g, d_S and d_u are required");
+    const int q = P->pmin - 2, nx = P->slab_nx, ny = P->slab_ny, s = P->slab_s;
+    const int n = ny * q, S = nx / s, sq = s * q, nxq = nx * q, nps = 2 * (s + ny) * q, ldt = nps + m;
+    const int c3 = (int)round_up(n, 4), lda = (int)round_up(c3 + 2 * n + m, 4);
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *th = (const double *)P->slab_th.p, *aug = (const double *)P->slab_aug.p;
+    double *t = (double *)P->slab_tmp.p;                    // n x m
+    double *vg = t + (size_t)n * m;                          // (S - 1) blocks n x m
+    double *u = vg + (size_t)S * n * m;                      // (S - 1) blocks n x m
+    double *ubs = u + (size_t)S * n * m;                     // S blocks nps x m
+    const double *gW = d_g, *gE = d_g + (size_t)n * m, *gS = d_g + (size_t)2 * n * m, *gN = gS + (size_t)nxq * m;
+    cudaError_t e = cudaSuccess;
+    int launches = 0;
+    auto gemv = [&](const double *A, long long la, int rows, int cols, const double *x, int ldx, double *y, double alpha,
+                    double beta, const double *add, int ldadd) {
+        if (e == cudaSuccess) e = launch_gemv(A, la, rows, cols, x, ldx, y, m, m, alpha, beta, add, ldadd, st);
+        ++launches;
+    };
+    // forward: v^g_k = G_k (b^g_k - L_k v^g_{k-1}), b^g_k from the outer data
+    for (int k = 0; k < S - 1; ++k) {
+        const double *Tk = th + (size_t)k * nps * ldt, *Tk1 = th + (size_t)(k + 1) * nps * ldt;
+        const double *TkE = Tk + (size_t)n * ldt;           // slab k, E rows
+        gemv(TkE + 2 * n, ldt, n, sq, gS + (size_t)k * sq * m, m, t, -1.0, 0.0, nullptr, 0);
+        gemv(TkE + 2 * n + sq, ldt, n, sq, gN + (size_t)k * sq * m, m, t, -1.0, 1.0, nullptr, 0);
+        gemv(Tk1 + 2 * n, ldt, n, sq, gS + (size_t)(k + 1) * sq * m, m, t, -1.0, 1.0, nullptr, 0);
+        gemv(Tk1 + 2 * n + sq, ldt, n, sq, gN + (size_t)(k + 1) * sq * m, m, t, -1.0, 1.0, nullptr, 0);
+        if (k == 0) gemv(TkE, ldt, n, n, gW, m, t, -1.0, 1.0, nullptr, 0);                 // outer W data
+        else gemv(TkE, ldt, n, n, vg + (size_t)(k - 1) * n * m, m, t, -1.0, 1.0, nullptr, 0);   // - L_k v^g_{k-1}
+        if (k == S - 2) gemv(Tk1 + n, ldt, n, n, gE, m, t, -1.0, 1.0, nullptr, 0);         // outer E data
+        gemv(aug + (size_t)k * n * lda + c3 + n, lda, n, n, t, m, vg + (size_t)k * n * m, 1.0, 0.0, nullptr, 0);
+    }
+    // back: u_k = v^g_k + v^h_k + S_k u_{k+1}
+    for (int k = S - 2; k >= 0; --k) {
+        const double *ak = aug + (size_t)k * n * lda;
+        double *uk = u + (size_t)k * n * m;
+        if (k == S - 2) gemv(ak, lda, n, 0, t, m, uk, 0.0, 0.0, vg + (size_t)k * n * m, m);
+        else gemv(ak + c3, lda, n, n, u + (size_t)(k + 1) * n * m, m, uk, 1.0, 0.0, vg + (size_t)k * n * m, m);
+        gemv(ak, lda, n, 0, t, m, uk, 0.0, 1.0, ak + c3 + 2 * n, lda);
+    }
+    // every slab's boundary values, the downward pass inside the slabs, the leaves
+    if (e == cudaSuccess) e = launch_slab_bounds(S, n, sq, nxq, m, u, d_g, ubs, st);
+    if (e == cudaSuccess) e = down_levels(P, ubs, (double *)P->u_leaf.p, st);
+    if (e == cudaSuccess) e = launch_leaf_recover(P->n_leaves, P->pmin, m, d_S, d_W, (const double *)P->u_leaf.p, d_u, st);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_slab_solve");
+    P->launches = launches + 2 + 2 * (int)P->levels.size();
+    return HPS_OK;
+}
+
 void hps_destroy(hps_plan *P) {
     if (P == nullptr) return;
     cudaDeviceSynchronize();
@@ -903,6 +1039,7 @@ void hps_destroy(hps_plan *P) {
         L.piv.release(); L.u3.release();
     }
     P->u_leaf.release();
+    P->slab_th.release(); P->slab_aug.release(); P->slab_piv.release(); P->slab_info.release(); P->slab_tmp.release();
     P->hstage.release();
     P->horder.release();
     for (cudaStream_t t : {P->hs_comp, P->hs_h2d, P->hs_d2h, P->split_aux.side})

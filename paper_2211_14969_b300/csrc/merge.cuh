@@ -34,6 +34,28 @@ struct SplitAux {
     cudaEvent_t a, b;
 };
 
+// One interface step of SlabLU's block LU (slab.cu): the augmented system
+// [Delta_k | 0 | -U_k | I | y_k] of interface k from the [T | h] maps of
+// the slabs on its two sides and the solved system of interface k - 1.
+struct SlabStepDev {
+    int n;      // interface nodes (ny q)
+    int m;      // body-load columns
+    int ldt;    // leading dimension of a slab's [T | h] (np + m)
+    int np;     // slab boundary nodes 2 (s + ny) q
+    int lda;    // leading dimension of the augmented systems
+    int c3;     // first right-hand column (round4(n))
+    int last;   // interface S-2: no right neighbour interface (U = 0)
+    const double *left, *right;   // [T | h] of slabs k and k + 1
+    const double *prev;           // solved system of interface k - 1, or null
+    double *aug;                  // this interface's augmented system
+};
+cudaError_t launch_slab_assemble(const SlabStepDev &S, cudaStream_t s);
+// y = beta y + alpha A x (+ add), A rows x cols (ld lda), x cols x m (ld ldx)
+cudaError_t launch_gemv(const double *A, long long lda, int rows, int cols, const double *x, int ldx, double *y,
+                        int ldy, int m, double alpha, double beta, const double *add, int ldadd, cudaStream_t s);
+cudaError_t launch_slab_bounds(int nslab, int n, int sq, int nxq, int m, const double *u, const double *g, double *ub,
+                               cudaStream_t s);
+
 cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s,
                                const SplitAux *aux = nullptr);
 // [Z | 0 | B] -> [U | 0 | X] for every merge of a level, one blocked-LU step

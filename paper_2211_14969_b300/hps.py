@@ -56,6 +56,8 @@ def load_library():
     L.hps_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.hps_merge_boxes.argtypes = [vp, i, i, i, i, vp, vp, i, vp, vp]
     L.hps_solve_boxes.argtypes = [vp, vp, i, vp, vp]
+    L.hps_slab_factor.argtypes = [vp, i, i, i, vp, vp, i, vp]
+    L.hps_slab_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
     L.hps_leaf_resolve.argtypes = [vp, i, vp, vp, i, vp, d, i, vp, vp, vp]
     L.hps_leaf_recover.argtypes = [vp, vp, vp, i, vp, vp, vp]
     L.hps_set_timing.argtypes = [vp, i]
@@ -71,7 +73,7 @@ def load_library():
     L.hps_destroy.restype = None
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_condense_host", "hps_merge", "hps_solve",
-                 "hps_merge_boxes", "hps_solve_boxes",
+                 "hps_merge_boxes", "hps_solve_boxes", "hps_slab_factor", "hps_slab_solve",
                  "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split",
                  "hps_fallback_count",
                  "hps_phase_times", "hps_last_launch_count"):
@@ -170,6 +172,22 @@ class Plan:
 
     def solve_boxes(self, g, m, out=None, stream=None):
         return hps_solve_boxes(self, g, m, out, stream)
+
+    def slab_factor(self, nx, ny, s, T, h, m, stream=None):
+        """SlabLU: slabs of s leaf columns, block LU of the interface system."""
+        _check_dev(T, "T", int(self.layout.o_bb[-1]))
+        self.check(load_library().hps_slab_factor(self.handle, int(nx), int(ny), int(s), _ptr(T), _ptr(h), int(m),
+                                                  _stream(stream)), "hps_slab_factor")
+
+    def slab_solve(self, g, S, W, m, out=None, stream=None):
+        import torch
+        _check_dev(g, "g")
+        _check_dev(S, "S", int(self.layout.o_sb[-1]))
+        u = out if out is not None else torch.empty(int(self.layout.o_p2[-1] * m), dtype=torch.float64,
+                                                    device=g.device)
+        self.check(load_library().hps_slab_solve(self.handle, _ptr(g), _ptr(S), _ptr(W), int(m), _ptr(u),
+                                                 _stream(stream)), "hps_slab_solve")
+        return u
 
     def leaf_resolve(self, coef, ub, f=None, m=None, prec="fp64", tol=1e-12, kmax=6, out=None, stream=None):
         return hps_leaf_resolve(self, coef, ub, f, m, prec, tol, kmax, out, stream)
