@@ -427,6 +427,151 @@ def key_coords(p, key, nx, ny, lx=1.0, ly=1.0, x0=0.0, y0=0.0):
 
 
 # ----------------------------------------------------------------------------
+# Impedance-to-impedance (ItI) leaf maps and merges.  Not in the paper (its
+# leaf maps are DtN maps, which do not exist when kappa^2 is an eigenvalue of
+# the leaf's Dirichlet problem); the impedance formulation of Gillman,
+# Barnett and Martinsson (BIT 2015), restated here from its definitions:
+# incoming data f = u_n + i eta u, outgoing data g = u_n - i eta u on a box
+# boundary (u_n the outward normal derivative, eta > 0), and the leaf
+# problem with the impedance condition is solvable at every real kappa.
+# ----------------------------------------------------------------------------
+
+
+def iti_leaf(p, box, coef, kappa, eta, f=None):
+    """ItI map of one leaf.  Unknowns: u at the interior and edge nodes
+    (corners are not unknowns, as for the DtN maps); rows: the PDE at the
+    interior nodes (corner columns folded in by interior_edge_block) and,
+    at every edge node a, the impedance condition (N u)_a + i eta u_a =
+    f_a.  With Y the solution for unit incoming data (one column per edge
+    node) and uf the solution for the body load with zero incoming data:
+        g = f - 2 i eta u_b   =>   R = I - 2 i eta Y_b,  h = -2 i eta uf_b.
+    Returns R (n_b x n_b), h (n_b x m), Y and uf over [interior; edge]
+    nodes (complex)."""
+    A, Nrow, _, _ = leaf_operator(p, box, coef, kappa)
+    ix = leaf_index_sets(p)
+    I, B = ix["I"], ix["B"]
+    ni, nb = len(I), len(B)
+    M = np.zeros((ni + nb, ni + nb), dtype=complex)
+    M[:ni, :ni] = A[np.ix_(I, I)]
+    M[:ni, ni:] = interior_edge_block(A, p)
+    M[ni:, :ni] = Nrow[:, I]
+    M[ni:, ni:] = Nrow[:, B] + 1j * eta * np.eye(nb)
+    m = 0 if f is None else np.asarray(f).reshape(p * p, -1).shape[1]
+    rhs = np.zeros((ni + nb, nb + m), dtype=complex)
+    rhs[ni:, :nb] = np.eye(nb)
+    if m:
+        rhs[:ni, nb:] = np.asarray(f, dtype=float).reshape(p * p, -1)[I]
+    sol = np.linalg.solve(M, rhs)
+    Y, uf = sol[:, :nb], sol[:, nb:]
+    return {"R": np.eye(nb) - 2j * eta * Y[ni:], "h": -2j * eta * uf[ni:], "Y": Y, "uf": uf, "M": M}
+
+
+def iti_merge_two(ka, Ra, ha, kb, Rb, hb, kpar):
+    """Merge the ItI maps of sibling boxes alpha, beta along their shared
+    edge 3.  On it the outward normals are opposite and u is continuous, so
+    the incoming data of one box is minus the outgoing data of the other:
+    f_a3 = -g_b3, f_b3 = -g_a3.  With t = g_a3:
+        (I - Ra33 Rb33) t = Ra31 f1 - Ra33 Rb32 f2 + ha3 - Ra33 hb3,
+        f_a3 = -Rb32 f2 + Rb33 t - hb3,   f_b3 = -t,
+        g1 = Ra11 f1 + Ra13 f_a3 + ha1,   g2 = Rb22 f2 + Rb23 f_b3 + hb2.
+    Returns the parent's R, h in kpar order and the maps from the parent's
+    incoming data [f1; f2] (order k12) to the children's incoming data on
+    edge 3 (Fa3, fa3, Fb3, fb3) for the downward pass."""
+    pa = {k: i for i, k in enumerate(ka)}
+    pb = {k: i for i, k in enumerate(kb)}
+    k3 = [k for k in ka if k in pb]
+    k1 = [k for k in ka if k not in pb]
+    k2 = [k for k in kb if k not in pa]
+    a1, a3 = [pa[k] for k in k1], [pa[k] for k in k3]
+    b2, b3 = [pb[k] for k in k2], [pb[k] for k in k3]
+    ix = np.ix_
+    n1, n2, n3 = len(k1), len(k2), len(k3)
+    Ra33, Rb33 = Ra[ix(a3, a3)], Rb[ix(b3, b3)]
+    K = np.eye(n3) - Ra33 @ Rb33
+    rhs = np.hstack([Ra[ix(a3, a1)], -Ra33 @ Rb[ix(b3, b2)], (ha[a3] - Ra33 @ hb[b3])])
+    X = np.linalg.solve(K, rhs)
+    T1, th = X[:, :n1 + n2], X[:, n1 + n2:]
+    Fa3 = np.hstack([np.zeros((n3, n1)), -Rb[ix(b3, b2)]]) + Rb33 @ T1
+    fa3 = Rb33 @ th - hb[b3]
+    Fb3, fb3 = -T1, -th
+    Rp = np.zeros((n1 + n2, n1 + n2), dtype=complex)
+    Rp[:n1, :n1] = Ra[ix(a1, a1)]
+    Rp[n1:, n1:] = Rb[ix(b2, b2)]
+    Rp[:n1] += Ra[ix(a1, a3)] @ Fa3
+    Rp[n1:] += Rb[ix(b2, b3)] @ Fb3
+    hp = np.vstack([ha[a1] + Ra[ix(a1, a3)] @ fa3, hb[b2] + Rb[ix(b2, b3)] @ fb3])
+    k12 = k1 + k2
+    pos = {k: i for i, k in enumerate(k12)}
+    perm = [pos[k] for k in kpar]
+    return {"R": Rp[ix(perm, perm)], "h": hp[perm], "k12": k12, "k3": k3,
+            "Fa3": Fa3, "fa3": fa3, "Fb3": Fb3, "fb3": fb3}
+
+
+def iti_solve(p, nx, ny, leaves, g_keys, eta):
+    """Merge the leaves' ItI maps over the grid (the schedule of hps_upward),
+    impose the Dirichlet data at the root (f - g = 2 i eta u there, so
+    (I - R) f = h + 2 i eta u_D), pass the incoming data down, and recover
+    every leaf's values u = Y f + uf.  leaves[ix * ny + iy] holds an
+    iti_leaf record.  Returns per leaf (u_b, u_i) as hps_downward does
+    (complex; real for real data)."""
+    boxes = {}
+    for ix in range(nx):
+        for iy in range(ny):
+            lf = leaves[ix * ny + iy]
+            boxes[(ix, iy)] = {"R": lf["R"], "h": lf["h"], "keys": box_keys(p, ix, iy, 1, 1)}
+    wx, wy = 1, 1
+    levels = []
+    for d in merge_schedule(nx, ny):
+        new = {}
+        for (ix0, iy0) in sorted(boxes):
+            if d == "x" and (ix0 // wx) % 2 == 0:
+                other = (ix0 + wx, iy0)
+                kpar = box_keys(p, ix0, iy0, 2 * wx, wy)
+            elif d == "y" and (iy0 // wy) % 2 == 0:
+                other = (ix0, iy0 + wy)
+                kpar = box_keys(p, ix0, iy0, wx, 2 * wy)
+            else:
+                continue
+            a, b = boxes[(ix0, iy0)], boxes[other]
+            rec = iti_merge_two(a["keys"], a["R"], a["h"], b["keys"], b["R"], b["h"], kpar)
+            rec["keys"] = kpar
+            rec["children"] = ((ix0, iy0), other)
+            new[(ix0, iy0)] = rec
+        wx, wy = (wx * 2, wy) if d == "x" else (wx, wy * 2)
+        boxes = new
+        levels.append(new)
+    root = boxes[(0, 0)]
+    keys = root["keys"]
+    uD = np.array([np.atleast_1d(g_keys[k]) for k in keys], dtype=complex)
+    f_root = np.linalg.solve(np.eye(len(keys)) - root["R"], root["h"] + 2j * eta * uD)
+    # incoming data per box, key -> value, from the root down: a child keeps
+    # the parent's data on its exterior edges and takes its own value on the
+    # shared edge (the two children see different incoming data there)
+    cur = {(0, 0): dict(zip(keys, f_root))}
+    for lev in reversed(levels):
+        nxt = {}
+        for o, rec in lev.items():
+            pf = cur[o]
+            f12 = np.array([pf[k] for k in rec["k12"]])
+            ca, cb = rec["children"]
+            fa = {k: v for k, v in pf.items()}
+            fb = dict(fa)
+            fa.update(zip(rec["k3"], rec["Fa3"] @ f12 + rec["fa3"]))
+            fb.update(zip(rec["k3"], rec["Fb3"] @ f12 + rec["fb3"]))
+            nxt[ca], nxt[cb] = fa, fb
+        cur = nxt
+    ni = len(leaf_index_sets(p)["I"])
+    out = []
+    for ix in range(nx):
+        for iy in range(ny):
+            lf = leaves[ix * ny + iy]
+            fl = np.array([cur[(ix, iy)][k] for k in box_keys(p, ix, iy, 1, 1)])
+            u = lf["Y"] @ fl + lf["uf"]
+            out.append({"u_b": u[ni:], "u_i": u[:ni], "f_in": fl})
+    return out
+
+
+# ----------------------------------------------------------------------------
 # SlabLU: the reduced system of Eq. (hps_reduced) in the slab block form of
 # Eq. (dell1); slab interiors eliminated, the block-tridiagonal interface
 # system factored densely (Section 2, the SlabLU paragraphs)

@@ -588,3 +588,116 @@ def test_slab_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(O, "reduced_system", flipped)
     with pytest.raises(AssertionError):
         test_slab_solve_equals_merge_tree_and_dense_solve(2)
+
+
+# --------------------------------------------- impedance-to-impedance maps
+
+def _analytic_flux(u, x, y, ix):
+    dudx, dudy = u(x, y, 1, 0), u(x, y, 0, 1)
+    return np.concatenate([-dudx[ix["W"]], dudx[ix["E"]], -dudy[ix["S"]], dudy[ix["N"]]])
+
+
+@pytest.mark.parametrize("c12", [False, True])
+def test_iti_leaf_manufactured(c12):
+    """A tensor polynomial with random coefficient samples: from its
+    incoming impedance data u_n + i eta u the leaf solve reproduces it at
+    every node, and R f + h is its outgoing data u_n - i eta u (u_n the
+    analytic outward normal derivative; degree p - 1, or p - 3 with the
+    corner extrapolation of the mixed term)."""
+    rng = np.random.default_rng(31)
+    p, box, kappa, eta = 9, (0.25, 0.5, 0.25, 0.125), 6.0, 4.0
+    deg = p - 3 if c12 else p - 1
+    u = random_poly(rng, deg, deg, xc=0.375, yc=0.5625, sx=0.125, sy=0.0625)
+    coef = random_coef(rng, p * p, c12=c12)
+    x, y = O.leaf_nodes(p, box)
+    f = u.apply_operator(x, y, coef, kappa)[:, None]
+    ix = O.leaf_index_sets(p)
+    out = O.iti_leaf(p, box, coef, kappa, eta, f)
+    uv = u(x, y)
+    dn = _analytic_flux(u, x, y, ix)
+    f_in = (dn + 1j * eta * uv[ix["B"]])[:, None]
+    sol = out["Y"] @ f_in + out["uf"]
+    assert np.abs(sol[: len(ix["I"]), 0] - uv[ix["I"]]).max() / np.abs(uv).max() < 1e-10
+    assert np.abs(sol[len(ix["I"]):, 0] - uv[ix["B"]]).max() / np.abs(uv).max() < 1e-10
+    g = out["R"] @ f_in + out["h"]
+    ref = dn - 1j * eta * uv[ix["B"]]
+    assert np.abs(g[:, 0] - ref).max() / np.abs(ref).max() < 1e-10
+
+
+def test_iti_is_the_cayley_transform_of_the_dtn_map():
+    """Where the DtN map exists: u_b = (T + i eta)^{-1} (f - h_D) gives
+    R = (T - i eta)(T + i eta)^{-1} and h = (I - R) h_D (an algebraic
+    identity between two independent computations)."""
+    rng = np.random.default_rng(5)
+    p, box, kappa, eta = 10, (0.0, 0.0, 0.125, 0.125), 20.0, 20.0
+    coef = random_coef(rng, p * p)
+    f = rng.standard_normal((p * p, 2))
+    d = O.condense_leaf(p, box, coef, kappa, f)
+    it = O.iti_leaf(p, box, coef, kappa, eta, f)
+    nb = d["T"].shape[0]
+    Rc = np.linalg.solve((d["T"] + 1j * eta * np.eye(nb)).T, (d["T"] - 1j * eta * np.eye(nb)).T).T
+    assert np.abs(it["R"] - Rc).max() / np.abs(Rc).max() < 1e-11
+    hc = (np.eye(nb) - Rc) @ d["h"]
+    assert np.abs(it["h"] - hc).max() / np.abs(hc).max() < 1e-11
+
+
+def _resonant_leaf_grid(p=8, n=2):
+    """An n x n grid of leaves with constant coefficients, b = 1 + 0.25 l on
+    leaf l, and kappa^2 the smallest eigenvalue of leaf 0's discrete
+    Dirichlet operator: leaf 0's A_ii is singular (a Dirichlet resonance),
+    the other leaves and the global problem are not."""
+    boxes = O.grid_boxes(n, n)
+    one, zero = np.ones(p * p), np.zeros(p * p)
+    coefs = [np.stack([one, zero, one, zero, zero, (1.0 + 0.25 * l) * one]) for l in range(n * n)]
+    A0, _, _, _ = O.leaf_operator(p, boxes[0], coefs[0], 0.0)
+    I = O.leaf_index_sets(p)["I"]
+    lam = np.linalg.eigvals(A0[np.ix_(I, I)])
+    return float(np.sqrt(np.min(lam.real))), coefs
+
+
+def test_iti_solves_through_leaf_resonances():
+    """A leaf at a Dirichlet resonance (cond(A_ii) ~ 1/eps, its DtN map does
+    not exist): the ItI merge and solve still equals the brute-force dense
+    solve of the global system."""
+    p, n = 8, 2
+    kappa, coefs = _resonant_leaf_grid(p, n)
+    boxes = O.grid_boxes(n, n)
+    I = O.leaf_index_sets(p)["I"]
+    A_ii = O.leaf_operator(p, boxes[0], coefs[0], kappa)[0][np.ix_(I, I)]
+    assert np.linalg.cond(A_ii) > 1e12
+    g_fn = lambda x, y: np.sin(kappa * (0.6 * x + 0.8 * y))
+    fs = [np.zeros((p * p, 1)) for _ in range(n * n)]
+    leaves = [O.iti_leaf(p, b, coefs[l], kappa, kappa, fs[l]) for l, b in enumerate(boxes)]
+    gk = {k: np.atleast_1d(g_fn(*O.key_coords(p, k, n, n))) for k in O.outer_boundary_keys(p, n, n)}
+    sol = O.iti_solve(p, n, n, leaves, gk, kappa)
+    dense, res = O.global_dense_solve(p, n, n, coefs, kappa, fs, g_fn)
+    assert res < 1e-12
+    ref = [(d["u_b"], d["u_i"]) for d in dense]
+    assert grid_error(sol, ref) < 1e-9
+    # the DtN merge tree on the same leaves loses its accuracy there
+    dl = [O.condense_leaf(p, b, coefs[l], kappa, fs[l]) for l, b in enumerate(boxes)]
+    dtn = O.hps_downward(p, n, n, O.hps_upward(p, n, n, dl), dl, gk)
+    assert grid_error(dtn, ref) > 1e-4
+
+
+def test_iti_solve_equals_merge_tree():
+    p = 10
+    w, coefs, fs = planewave_case(p, 4, 4)
+    sol, _ = hps_grid_solve(p, 4, 4, coefs, w.kappa, fs, w.dirichlet_data)
+    boxes = O.grid_boxes(4, 4)
+    leaves = [O.iti_leaf(p, boxes[l], coefs[l], w.kappa, w.kappa, fs[l]) for l in range(16)]
+    gk = {k: np.atleast_1d(w.dirichlet_data(*O.key_coords(p, k, 4, 4))) for k in O.outer_boundary_keys(p, 4, 4)}
+    it = O.iti_solve(p, 4, 4, leaves, gk, w.kappa)
+    assert grid_error(it, [(d["u_b"], d["u_i"]) for d in sol]) < 1e-12
+
+
+def test_iti_planted_sign_is_caught(monkeypatch):
+    """Incoming data on the shared edge taken as +g of the other box (the
+    normals' opposition dropped) breaks the merged solve."""
+    real = O.iti_merge_two
+
+    def wrong(ka, Ra, ha, kb, Rb, hb, kpar):
+        return real(ka, Ra, ha, kb, -Rb, -hb, kpar)
+    monkeypatch.setattr(O, "iti_merge_two", wrong)
+    with pytest.raises(AssertionError):
+        test_iti_solve_equals_merge_tree()
