@@ -135,6 +135,28 @@ hps_status hps_condense(hps_plan *plan, hps_prec prec, const double *d_coef, con
                         int m, double tol, int kmax, double *d_S, double *d_T, double *d_h,
                         double *d_W, int *d_info, hps_stream stream);
 
+/* Impedance-to-impedance (ItI) leaf maps, in place of the DtN maps of
+ * hps_condense where a leaf may sit at an interior Dirichlet resonance
+ * (kappa^2 an eigenvalue of its Dirichlet problem: A_ii singular, no DtN
+ * map).  Not in the paper; the impedance formulation of Gillman, Barnett
+ * and Martinsson (BIT 2015), from its definitions: on a box boundary the
+ * incoming data is f = u_n + i eta u and the outgoing data g = u_n - i eta u
+ * (u_n the outward normal derivative, eta > 0, typically kappa).  Per leaf
+ * the collocation system with the impedance condition on every edge node
+ * (the PDE rows at the interior nodes as in hps_condense, corner columns
+ * folded in the same way) is solved in FP64 (complex, assembled in real
+ * form of twice the size): with Y the values for unit incoming data and uf
+ * those for the body loads with zero incoming data,
+ *   R = I - 2 i eta Y_b   (n_b x n_b),   h = -2 i eta uf_b   (n_b x m),
+ * so g = R f + h, and the interior values are u_i = Y_i f + uf_i.
+ * Outputs are complex, interleaved (re, im), packed as hps_condense's with
+ * twice the element count: d_R like T, d_h like h (required when m > 0),
+ * d_Y like S (may be NULL), d_uf like W (may be NULL); d_info as
+ * hps_condense (k > 0: exact zero pivot at step k of the real-form LU).
+ * d_coef, d_f as hps_condense.  HPS_ERR_ARG for eta <= 0. */
+hps_status hps_iti_condense(hps_plan *plan, double eta, const double *d_coef, const double *d_f, int m, double *d_R,
+                            double *d_h, double *d_Y, double *d_uf, int *d_info, hps_stream stream);
+
 /* Maximum pipeline depth of hps_condense_host. */
 #define HPS_HOST_MAX_CHUNKS 64
 
@@ -347,7 +369,7 @@ const char *hps_last_error(const hps_plan *plan);
 void hps_destroy(hps_plan *plan);
 
 /* ABI version: major * 100 + minor (1.01: hps_merge_boxes, hps_solve_boxes;
- * 1.02: hps_slab_factor, hps_slab_solve). */
+ * 1.02: hps_slab_factor, hps_slab_solve; 1.03: hps_iti_condense). */
 int hps_version(void);
 
 #ifdef __cplusplus

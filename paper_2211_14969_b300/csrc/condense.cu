@@ -899,6 +899,166 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
     if constexpr (TCK != 0) tc::tmem_free(tcs);
 }
 
+// ---------------------------------------------------------------------------
+// Impedance-to-impedance leaf maps.  The leaf system with the impedance
+// condition (N u)_a + i eta u_a = f_a at every edge node a (the PDE rows at
+// the interior nodes as for the DtN maps, corners folded into the edge
+// columns) is complex; it is assembled in real form over the unknowns
+// [Re u_i (n) | Re u_b (nb) | Im u_i (n) | Im u_b (nb)] with the rows in the
+// same order (PDE, impedance; real parts, then imaginary parts) and solved
+// by the FP64 blocked LU for nb unit incoming-data columns and the m body
+// loads.  Y = X_re + i X_im; R = I - 2 i eta Y_b, h = -2 i eta uf_b.
+// ---------------------------------------------------------------------------
+
+struct ItiInfo {
+    int N, R2, n4, C, LDC;   // N = n + nb unknowns per part, R2 = 2N real rows
+};
+
+__device__ ItiInfo iti_info(const LeafInfo &L) {
+    ItiInfo I;
+    I.N = L.n + L.nbd;
+    I.R2 = 2 * I.N;
+    I.n4 = (I.R2 + 3) & ~3;
+    I.C = I.n4 + L.nbd + L.m;
+    I.LDC = (I.C + 3) & ~3;
+    return I;
+}
+
+// One warp per real row: zero the row, then its entries.
+__device__ void assemble_iti(double *__restrict__ M, const LeafInfo &L, const ItiInfo &I, const double *__restrict__ D,
+                             double kappa2, double eta) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = L.p, q = L.q, p2 = p * p, n = L.n, N = I.N;
+    const double *D2 = D + p2, *cw = D2 + p2;
+    const bool dense = (L.flags & 1) != 0;
+    for (int row = warp; row < I.R2; row += NWARP) {
+        double *r = M + (long long)row * I.LDC;
+        for (int c = lane * 2; c < I.LDC; c += 64) *(double2 *)(r + c) = make_double2(0.0, 0.0);
+        __syncwarp();
+        const int part = row / N, rr = row - part * N;   // part 0: real rows, 1: imaginary rows
+        const int off = part * N;                         // their unknowns' columns
+        if (rr < n) {
+            // PDE at interior node (i, j): A_ii into [off, off + n), A_ib into [off + n, off + N)
+            const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
+            const double ax2 = L.coef[node] * L.sx * L.sx, ax1 = L.coef[3 * p2 + node] * L.sx;
+            const double ay2 = L.coef[2 * p2 + node] * L.sy * L.sy, ay1 = L.coef[4 * p2 + node] * L.sy;
+            const double axy = 2.0 * L.coef[p2 + node] * L.sx * L.sy, dg = kappa2 * L.coef[5 * p2 + node];
+            // corner values of the mixed term: corner (k, l) with k, l in {0, p-1}
+            const double c00 = -(axy * D[i * p] * D[j * p]), c0P = -(axy * D[i * p] * D[j * p + p - 1]);
+            const double cP0 = -(axy * D[i * p + p - 1] * D[j * p]), cPP = -(axy * D[i * p + p - 1] * D[j * p + p - 1]);
+            for (int e = lane; e < p2; e += 32) {
+                const int k = e / p, l = e - k * p;
+                const bool bk = (k == 0 || k == p - 1), bl = (l == 0 || l == p - 1);
+                if (bk && bl) continue;                                   // corners are not unknowns
+                if (!dense && k != i && l != j) continue;                 // off the two grid lines: zero
+                double v = 0.0;
+                if (l == j) v += ax2 * D2[i * p + k] + ax1 * D[i * p + k];
+                if (k == i) v += ay2 * D2[j * p + l] + ay1 * D[j * p + l];
+                if (dense) v += axy * D[i * p + k] * D[j * p + l];
+                v = -v;
+                if (k == i && l == j) v -= dg;
+                if (!bk && !bl) {
+                    r[off + (k - 1) * q + (l - 1)] = v;
+                } else {
+                    if (dense) {   // the corners at the ends of this edge node's edge (mean extrapolation)
+                        if (bk) v += cw[l] * (k == 0 ? c00 : cP0) + cw[p + l] * (k == 0 ? c0P : cPP);
+                        else v += cw[k] * (l == 0 ? c00 : c0P) + cw[p + k] * (l == 0 ? cP0 : cPP);
+                    }
+                    r[off + n + edge_index(k, l, p, q)] = v;
+                }
+            }
+            if (part == 0 && L.f)
+                for (int c = lane; c < L.m; c += 32) r[I.n4 + L.nbd + c] = L.f[(long long)node * L.m + c];
+        } else {
+            // impedance condition at edge node a: the outward normal derivative
+            // along the grid line through a, plus i eta u_a
+            const int a = rr - n, edge = a / q, s = a - edge * q;
+            const bool far = (edge & 1);
+            const double scl = (far ? 1.0 : -1.0) * ((edge < 2) ? L.sx : L.sy);
+            const double *Drow = D + (far ? (p - 1) * p : 0);
+            const int lo = (edge < 2) ? s : 2 * q + s, hi = (edge < 2) ? q + s : 3 * q + s;   // W/S and E/N ends
+            for (int k = lane; k < p; k += 32) {
+                const double v = scl * Drow[k];
+                if (k == 0) r[off + n + lo] += v;
+                else if (k == p - 1) r[off + n + hi] += v;
+                else r[off + ((edge < 2) ? (k - 1) * q + s : s * q + (k - 1))] = v;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                if (part == 0) {
+                    r[N + n + a] = -eta;           // Re: (N u_re) - eta u_im = Re f
+                    r[I.n4 + a] = 1.0;             // unit incoming data, real
+                } else {
+                    r[n + a] = eta;                // Im: (N u_im) + eta u_re = Im f
+                }
+            }
+        }
+    }
+}
+
+// Outputs from X = M[:, n4 ..] (2N x (nb + m)), complex interleaved (re, im):
+// R [nb][nb], h [nb][m], and for the interior recovery Y_i [n][nb], uf_i [n][m].
+__device__ void write_iti(const CondenseParams &P, int leaf, const LeafInfo &L, const ItiInfo &I,
+                          const double *__restrict__ M) {
+    const int n = L.n, nb = L.nbd, m = L.m, N = I.N;
+    const double e2 = 2.0 * P.eta;
+    double *R = P.T + 2 * P.lt.o_bb[leaf];
+    double *h = (m > 0 && P.h) ? P.h + 2 * P.lt.o_nb[leaf] * m : nullptr;
+    double *Y = P.S ? P.S + 2 * P.lt.o_sb[leaf] : nullptr;
+    double *uf = (m > 0 && P.W) ? P.W + 2 * P.lt.o_ni[leaf] * m : nullptr;
+    const int cols = nb + m;
+    for (int e = threadIdx.x; e < N * cols; e += NT) {
+        const int row = e / cols, c = e - row * cols;
+        const double xr = M[(long long)row * I.LDC + I.n4 + c];
+        const double xi = M[(long long)(N + row) * I.LDC + I.n4 + c];
+        if (row >= n) {
+            const int a = row - n;
+            if (c < nb) {   // R = I - 2 i eta Y_b
+                R[2 * ((long long)a * nb + c)] = (a == c ? 1.0 : 0.0) + e2 * xi;
+                R[2 * ((long long)a * nb + c) + 1] = -e2 * xr;
+            } else if (h) {
+                h[2 * ((long long)a * m + c - nb)] = e2 * xi;
+                h[2 * ((long long)a * m + c - nb) + 1] = -e2 * xr;
+            }
+        } else if (c < nb) {
+            if (Y) {
+                Y[2 * ((long long)row * nb + c)] = xr;
+                Y[2 * ((long long)row * nb + c) + 1] = xi;
+            }
+        } else if (uf) {
+            uf[2 * ((long long)row * m + c - nb)] = xr;
+            uf[2 * ((long long)row * m + c - nb) + 1] = xi;
+        }
+    }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NT, 4) iti_kernel(CondenseParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem<double> sm = carve<double, NB>(smem_raw, P.blk.ldp);
+    double *M = (double *)(P.work + (long long)blockIdx.x * P.slot_bytes);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(P.queue, 1);
+            sm.misc[0] = t < P.n_leaves ? P.lt.order[t] : -1;
+            sm.misc[1] = 0;
+        }
+        __syncthreads();
+        const int leaf = sm.misc[0];
+        if (leaf < 0) break;
+        LeafInfo L = leaf_info(P, leaf);
+        L.flags = leaf_flags(L);
+        const ItiInfo I = iti_info(L);
+        assemble_iti(M, L, I, P.dt.dmat + P.dt.doff[L.p], P.kappa2, P.eta);
+        __syncthreads();
+        lu_solve<double, NB>(M, I.LDC, I.R2, I.n4, I.C, true, nullptr, P.blk.ldp, sm);
+        write_iti(P, leaf, L, I, M);
+        __syncthreads();
+        if (threadIdx.x == 0) P.info[leaf] = sm.misc[1];
+        __syncthreads();
+    }
+}
+
 template <int NB>
 __global__ void __launch_bounds__(NT) dense_solve_kernel(double *base, long long stride, int n, int n4, int C,
                                                        int LDC, int ldp, int *info) {
@@ -1054,6 +1214,43 @@ int condense_max_ctas_per_sm(int prec, const LuBlocking &b) {
             return nb == 32 ? occupancy(condense_kernel<float, 32, true>, smem)
                  : nb == 16 ? occupancy(condense_kernel<float, 16, true>, smem) : occupancy(condense_kernel<float, 8, true>, smem);
     }
+}
+
+LuBlocking iti_blocking(int nmax_real) {
+    LuBlocking b;
+    b.ldp = panel_ld(nmax_real);
+    b.nb_panel = smem_of<double, 16>(b.ldp) <= 75 * 1024 ? 16 : smem_of<double, 8>(b.ldp) <= 75 * 1024 ? 8 : 4;
+    return b;
+}
+
+static size_t iti_smem(const LuBlocking &b) {
+    return b.nb_panel == 16 ? smem_of<double, 16>(b.ldp) : b.nb_panel == 8 ? smem_of<double, 8>(b.ldp)
+                                                                            : smem_of<double, 4>(b.ldp);
+}
+
+int iti_max_ctas_per_sm(const LuBlocking &b) {
+    const size_t smem = iti_smem(b);
+    return b.nb_panel == 16 ? occupancy(iti_kernel<16>, smem)
+         : b.nb_panel == 8 ? occupancy(iti_kernel<8>, smem) : occupancy(iti_kernel<4>, smem);
+}
+
+cudaError_t launch_iti(const CondenseParams &prm, int grid, cudaStream_t s) {
+    const size_t smem = iti_smem(prm.blk);
+    cudaError_t e = cudaSuccess;
+    switch (prm.blk.nb_panel) {
+        case 16:
+            e = cudaFuncSetAttribute(iti_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) iti_kernel<16><<<grid, NT, smem, s>>>(prm);
+            break;
+        case 8:
+            e = cudaFuncSetAttribute(iti_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) iti_kernel<8><<<grid, NT, smem, s>>>(prm);
+            break;
+        default:
+            e = cudaFuncSetAttribute(iti_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) iti_kernel<4><<<grid, NT, smem, s>>>(prm);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_condense(int prec, const CondenseParams &prm, int grid, cudaStream_t s) {

@@ -181,7 +181,7 @@ struct hps_plan {
 
 extern "C" {
 
-int hps_version(void) { return 102; }
+int hps_version(void) { return 103; }
 
 const char *hps_last_error(const hps_plan *plan) {
     if (plan == nullptr) return g_build_error.c_str();
@@ -578,6 +578,52 @@ hps_status hps_condense_host(hps_plan *P, hps_prec prec, const double *h_coef, c
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_back(nc - 1), 0);
     if (e != cudaSuccess) return P->cuda_fail(e, "hps_condense_host");
     P->launches = nc;
+    return HPS_OK;
+}
+
+hps_status hps_iti_condense(hps_plan *P, double eta, const double *d_coef, const double *d_f, int m, double *d_R,
+                            double *d_h, double *d_Y, double *d_uf, int *d_info, hps_stream stream) {
+    if (P == nullptr) return HPS_ERR_ARG;
+    if (!(eta > 0.0) || !std::isfinite(eta)) return P->fail(HPS_ERR_ARG, "hps_iti_condense: eta must be positive");
+    if (m < 0 || d_coef == nullptr || d_R == nullptr || d_info == nullptr || (m > 0 && (d_f == nullptr || d_h == nullptr)))
+        return P->fail(HPS_ERR_ARG, "hps_iti_condense: d_coef, d_R, d_info (and d_f, d_h when m > 0) are required");
+    const int qmax = P->pmax - 2;
+    const LuBlocking blk = iti_blocking(2 * (qmax * qmax + 4 * qmax));
+    const int per_sm = iti_max_ctas_per_sm(blk);
+    if (per_sm < 1) return P->fail(HPS_ERR_CUDA, "hps_iti_condense: kernel does not fit on an SM");
+    const int grid = std::min(P->n_leaves, P->sms * per_sm);
+    long long slot = 0;
+    for (int p = P->pmin; p <= P->pmax; ++p) {
+        const long long q = p - 2, N = q * q + 4 * q, n4 = round_up(2 * N, 4), LDC = round_up(n4 + 4 * q + m, 4);
+        slot = std::max(slot, round_up(2 * N * LDC * 8, 256));
+    }
+    cudaError_t e = P->work.ensure((size_t)slot * grid);
+    if (e != cudaSuccess) return P->cuda_fail(e, "hps_iti_condense: workspace");
+    CondenseParams prm{};
+    prm.blk = blk;
+    prm.lt = P->leaf_tables();
+    prm.dt.dmat = P->d_dmat;
+    prm.dt.dmat32 = P->d_dmat32;
+    prm.dt.dmat_lo = P->d_dmat_lo;
+    prm.dt.doff = P->d_doff;
+    prm.n_leaves = P->n_leaves;
+    prm.m = m;
+    prm.kappa2 = P->kappa * P->kappa;
+    prm.coef = d_coef;
+    prm.f = m > 0 ? d_f : nullptr;
+    prm.S = d_Y;
+    prm.T = d_R;
+    prm.h = m > 0 ? d_h : nullptr;
+    prm.W = m > 0 ? d_uf : nullptr;
+    prm.info = d_info;
+    prm.work = (unsigned char *)P->work.p;
+    prm.slot_bytes = slot;
+    prm.queue = P->d_queue;
+    prm.eta = eta;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((e = cudaMemsetAsync(P->d_queue, 0, sizeof(int), s)) != cudaSuccess) return P->cuda_fail(e, "hps_iti_condense");
+    if ((e = launch_iti(prm, grid, s)) != cudaSuccess) return P->cuda_fail(e, "hps_iti_condense: launch");
+    P->launches = 1;
     return HPS_OK;
 }
 

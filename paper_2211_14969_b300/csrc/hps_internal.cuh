@@ -62,6 +62,9 @@ struct CondenseParams {
     // solution at the nodes [p*p][m]; ub == nullptr condenses instead
     const double *ub;
     double *u;
+    // impedance-to-impedance maps (hps_iti_condense): eta of the impedance
+    // data u_n + i eta u; S, T, h, W then receive Y_i, R, h, uf_i (complex)
+    double eta;
 };
 
 // Host-side launchers (condense.cu).
@@ -70,6 +73,10 @@ size_t condense_smem(int prec, const LuBlocking &b);
 int condense_max_ctas_per_sm(int prec, const LuBlocking &b);
 cudaError_t launch_condense(int prec, const CondenseParams &prm, int grid, cudaStream_t s);
 cudaError_t launch_leaf_nodes(const LeafTables &lt, int n_leaves, double *xy, cudaStream_t s);
+// Impedance-to-impedance leaf maps (condense.cu: iti_kernel), FP64 real form.
+LuBlocking iti_blocking(int nmax_real);
+int iti_max_ctas_per_sm(const LuBlocking &b);
+cudaError_t launch_iti(const CondenseParams &prm, int grid, cudaStream_t s);
 cudaError_t launch_leaf_recover_all(const LeafTables &lt, int n_leaves, int m, const double *S, const double *W,
                                     const double *ub, double *u, cudaStream_t s);
 

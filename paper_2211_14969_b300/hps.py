@@ -58,6 +58,7 @@ def load_library():
     L.hps_solve_boxes.argtypes = [vp, vp, i, vp, vp]
     L.hps_slab_factor.argtypes = [vp, i, i, i, vp, vp, i, vp]
     L.hps_slab_solve.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    L.hps_iti_condense.argtypes = [vp, d, vp, vp, i, vp, vp, vp, vp, vp, vp]
     L.hps_leaf_resolve.argtypes = [vp, i, vp, vp, i, vp, d, i, vp, vp, vp]
     L.hps_leaf_recover.argtypes = [vp, vp, vp, i, vp, vp, vp]
     L.hps_set_timing.argtypes = [vp, i]
@@ -73,7 +74,7 @@ def load_library():
     L.hps_destroy.restype = None
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_condense_host", "hps_merge", "hps_solve",
-                 "hps_merge_boxes", "hps_solve_boxes", "hps_slab_factor", "hps_slab_solve",
+                 "hps_merge_boxes", "hps_solve_boxes", "hps_slab_factor", "hps_slab_solve", "hps_iti_condense",
                  "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split",
                  "hps_fallback_count",
                  "hps_phase_times", "hps_last_launch_count"):
@@ -178,6 +179,29 @@ class Plan:
         _check_dev(T, "T", int(self.layout.o_bb[-1]))
         self.check(load_library().hps_slab_factor(self.handle, int(nx), int(ny), int(s), _ptr(T), _ptr(h), int(m),
                                                   _stream(stream)), "hps_slab_factor")
+
+    def iti_condense(self, coef, f=None, m=None, eta=None, store_Y=True, stream=None):
+        """Impedance-to-impedance leaf maps: dict(R, h, Y, uf, info), complex
+        tensors (complex128) packed like T, h, S, W."""
+        import torch
+        lay = self.layout
+        if m is None:
+            m = 0 if f is None else int(f.numel() // int(lay.o_p2[-1]))
+        eta = self.kappa if eta is None else float(eta)
+        _check_dev(coef, "coef", int(6 * lay.o_p2[-1]))
+        _check_dev(f, "f", int(lay.o_p2[-1] * m) if f is not None else None)
+        dev = coef.device
+        z = lambda n: torch.empty(int(n) * 2, dtype=torch.float64, device=dev)
+        o = {"R": z(lay.o_bb[-1]), "info": torch.empty(lay.n_leaves, dtype=torch.int32, device=dev)}
+        if m > 0:
+            o["h"] = z(lay.o_nb[-1] * m)
+            o["uf"] = z(lay.o_ni[-1] * m)
+        if store_Y:
+            o["Y"] = z(lay.o_sb[-1])
+        self.check(load_library().hps_iti_condense(self.handle, float(eta), _ptr(coef), _ptr(f), int(m), _ptr(o["R"]),
+                                                   _ptr(o.get("h")), _ptr(o.get("Y")), _ptr(o.get("uf")),
+                                                   _ptr(o["info"]), _stream(stream)), "hps_iti_condense")
+        return {k: (torch.view_as_complex(v.view(-1, 2)) if k != "info" else v) for k, v in o.items()}
 
     def slab_solve(self, g, S, W, m, out=None, stream=None):
         import torch
