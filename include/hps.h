@@ -114,11 +114,17 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
  *       mixed paths refine to the same tolerance and need 4(p-2) + m <= 256
  *       for the largest p.
  * tol, kmax: iterative refinement with FP64 residuals.  Per right-hand column
- *            let eta_k = max|correction_k| / max|X| (eta_0 = 1); the error
- *            left after correction k is estimated as eta_k^2 / eta_{k-1}
- *            (linear convergence).  Refinement stops once every column's
- *            estimate is <= tol while still contracting, or after kmax
- *            corrections.  kmax = 0 returns the FP32 solution unrefined.
+ *            let eta_k = max|correction_k| / max|X| and r_k = max|R_k|, R_k
+ *            the residual of the iterate after k corrections.  After the
+ *            first correction the error left is estimated from the true
+ *            residuals as eta_1 r_1 / r_0 (the first correction measured the
+ *            unrefined error; the residual ratio is how much of it it
+ *            removed); after correction k >= 2 as eta_k^2 / eta_{k-1} (the
+ *            ratio of successive corrections measures the contraction).
+ *            Refinement stops once every column's estimate is <= tol (the
+ *            latter while still contracting), or after kmax corrections.
+ *            kmax = 0 returns the FP32 solution unrefined; with kmax = 1
+ *            the single correction is accepted by the eta_1^2 estimate.
  *            A leaf that does not converge (typically cond(A_ii) u_fp32
  *            near 1, e.g. close to an interior Dirichlet resonance) is
  *            condensed again in FP64 inside the same launch and gets the

@@ -358,7 +358,8 @@ template <typename T, bool GENERAL, bool RESOLVE = false>
 __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const LeafInfo &L,
                          const float *__restrict__ Dh, const float *__restrict__ Dl,
                          const float *__restrict__ nf, float *__restrict__ Xs, float2 *__restrict__ Dp,
-                         int cw_max, const double *__restrict__ ub = nullptr, bool sep = false) {
+                         int cw_max, const double *__restrict__ ub = nullptr, bool sep = false,
+                         unsigned *__restrict__ rmax = nullptr) {
     constexpr int G = 4;
     const int p = L.p, q = L.q, r = L.r, nbd = L.nbd, n = L.n, p2 = p * p;
     for (int e = threadIdx.x; e < 2 * p2; e += NT) Dp[e] = make_float2(Dh[e], Dl[e]);
@@ -426,6 +427,10 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
             }
             __syncthreads();
         }
+        // each thread's column group is the same in every pass of this
+        // loop (NT is a multiple of ng), so its column maxima of |R| are
+        // kept in registers and folded into rmax once per chunk
+        float rloc[G] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int w = threadIdx.x; w < n * ng; w += NT) {
             const int rr = w / ng, g = w - rr * ng;
             const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
@@ -553,7 +558,18 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                     au.hi = s2;
                     au.lo = __fadd_rn(au.lo, __fadd_rn(se, b.lo));
                 }
-                M[(long long)rr * L.LDC + L.n4 + c] = (T)__fadd_rn(au.hi, au.lo);
+                const float rv = __fadd_rn(au.hi, au.lo);
+                M[(long long)rr * L.LDC + L.n4 + c] = (T)rv;
+                rloc[t] = fmaxf(rloc[t], fabsf(rv));
+            }
+        }
+        if (rmax && threadIdx.x < n * ng) {
+            const int g = threadIdx.x % ng;
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const int cc = g * G + t;
+                if (cc < cw)   // non-negative floats order like their bit patterns; NaN maps high
+                    atomicMax(&rmax[c0 + cc], rloc[t] == rloc[t] ? __float_as_uint(rloc[t]) : 0x7f800000u);
             }
         }
         __syncthreads();
@@ -692,7 +708,7 @@ __device__ void write_u(const CondenseParams &P, int leaf, const LeafInfo &L, co
 // eta_k^2 / eta_{k-1}, and a column that stopped contracting never passes.
 template <typename T>
 __device__ bool refine_update(T *__restrict__ M, float2 *__restrict__ X, float *__restrict__ eta,
-                              const LeafInfo &L, double tol, unsigned *colmax) {
+                              const LeafInfo &L, double tol, unsigned *colmax, bool allow_stop = true) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = L.r;
     for (int c = threadIdx.x; c < 2 * r; c += NT) colmax[c] = 0u;
@@ -743,6 +759,21 @@ __device__ bool refine_update(T *__restrict__ M, float2 *__restrict__ X, float *
         const double est = e_prev > 0.0f ? (double)e_k * (double)e_k / (double)e_prev : 0.0;
         if (!(contracting && est <= tol)) bad = 1;
         eta[c] = e_k;
+    }
+    return __syncthreads_or(bad) == 0 && allow_stop;
+}
+
+// The first correction's stop: X_1's error estimated per column from the
+// true residuals as eta_1 |R_1| / |R_0| (the correction eta_1 measured X_0's
+// error; the residual ratio measures how much of it the correction
+// removed).  Block-uniform; rn0, rn1 hold |R_0|, |R_1| per column (float bit
+// patterns, from residual).
+__device__ bool residual_ratio_ok(const unsigned *rn1, const unsigned *rn0, const float *eta, int r, double tol) {
+    int bad = 0;
+    for (int c = threadIdx.x; c < r; c += NT) {
+        const float r1 = __uint_as_float(rn1[c]), r0 = __uint_as_float(rn0[c]);
+        const double est = r0 > 0.0f ? (double)eta[c] * (double)r1 / (double)r0 : 0.0;
+        if (!(est <= tol)) bad = 1;
     }
     return __syncthreads_or(bad) == 0;
 }
@@ -811,7 +842,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             int *perm_g = (int *)(X + (long long)L.n * L.r);   // 3 NB ints per panel
             lu_solve<T, NB, TCK, INV>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm, tsp);
             float *eta = (float *)(perm_g + 3 * (L.n + 64));
-            float *nf = eta + ((L.r + 63) & ~63);                 // 12 floats per interior node
+            unsigned *rn0 = (unsigned *)(eta + ((L.r + 63) & ~63));   // column max |R_0|, |R_1| (float bits)
+            unsigned *rn1 = rn0 + ((L.r + 63) & ~63);
+            float *nf = (float *)(rn1 + ((L.r + 63) & ~63));      // 12 floats per interior node
             const float *Dhi = P.dt.dmat32 + P.dt.doff[L.p], *Dlo = P.dt.dmat_lo + P.dt.doff[L.p];
             node_factors(L, P.kappa2, nf);
             // residual column chunk: as many FP64 columns as the panel and
@@ -854,14 +887,25 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             if (status == 0 && P.kmax > 0) {
                 int it = 0;
                 bool done = false;
+                for (int c = threadIdx.x; c < L.r; c += NT) rn0[c] = rn1[c] = 0u;
+                __syncthreads();
                 while (!done && it < P.kmax) {
                     float *xs = (float *)((float2 *)sm.Ps + 2 * L.p * L.p);
-                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl, sep);
-                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, sep);
-                    else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
+                    // the first two residuals also record their column maxima
+                    unsigned *rm = it == 0 ? rn0 : it == 1 ? rn1 : nullptr;
+                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl, sep, rm);
+                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, sep, rm);
+                    else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, false, rm);
                     __syncthreads();
+                    // after the first correction the true residual decides
+                    // whether X_1 is already good enough
+                    if (it == 1 && residual_ratio_ok(rn1, rn0, eta, L.r, P.tol)) {
+                        done = true;
+                        break;
+                    }
                     lu_solve<T, NB, 0, INV>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
-                    done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us);
+                    // the correction-ratio estimate stops from the second correction on
+                    done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us, it >= 1 || P.kmax == 1);
                     ++it;
                 }
                 if (!done) status = -it;
