@@ -805,6 +805,12 @@ def run_gpu(args, rank, ws):
                "api": "hps_condense_host, pinned host buffers, 8 chunks (copies overlap the launches)",
                "value_one_chunk": rates[1], "equals_device_call": bool(same)}
 
+    # the impedance-to-impedance leaf maps on the same leaves (FP64; the
+    # complex leaf system in real form, 2(n_i + n_b) unknowns)
+    iti = None
+    if rank == 0 and ws == 1 and not args.no_extra:
+        iti = iti_timing(w, plan, coef, f, max(3, args.steps // 3), 3, ws)
+
     per_order = None
     if args.workload == "uneven" and rank == 0:
         per_order = per_order_launches(w, plan, coef, f, res, max(2, args.steps // 2))
@@ -884,6 +890,8 @@ def run_gpu(args, rank, ws):
             line["reduced_solve_fp64"] = reduced
         if per_order is not None:
             line["per_order_launches"] = per_order
+        if iti is not None:
+            line["iti_fp64_path"] = iti
     plan.close()
     del outs
     torch.cuda.empty_cache()
@@ -967,6 +975,33 @@ def merge_flops(q, nx, ny, m):
         levels.append({"merges": nm, "n3": n3, "n_parent": npar, "gflop": f / 1e9})
         total += f
     return total, levels
+
+
+def iti_leaf_flops(p, m):
+    """Algorithmic flops of one ItI leaf map as computed: the LU of the real
+    form of the complex leaf system (2N unknowns, N = n_i + n_b) and its
+    solve for n_b + m right-hand columns."""
+    q = p - 2
+    n2 = 2 * (q * q + 4 * q)
+    return (2.0 / 3.0) * n2 ** 3 + 2.0 * n2 ** 2 * (4 * q + m)
+
+
+def iti_timing(w, plan, coef, f, steps, warmup, ws):
+    """hps_iti_condense over all the workload's leaves, eta = kappa."""
+    import torch
+    stream = torch.cuda.current_stream()
+    with ClockSampler(gpu_uuid()) as cs:
+        ms = time_steps(lambda: plan.iti_condense(coef, f, m=w.m, eta=w.kappa, store_Y=True), steps, warmup, ws,
+                        stream)
+    out = plan.iti_condense(coef, f, m=w.m, eta=w.kappa)
+    torch.cuda.synchronize()
+    flops = float(sum(iti_leaf_flops(int(p), w.m) for p in w.p))
+    tf = flops / (ms / steps * 1e-3) / 1e12
+    return {"value": w.n_leaves / (ms / steps * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "tflops": tf,
+            "dtype": "f64 (complex leaf system in real form)", "eta": w.kappa,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s", "frac": tf / 1.25,
+                         "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
+            "info_nonzero": int((out["info"] != 0).sum()), "gpu_launches": steps, "clocks": cs.summary()}
 
 
 def slab_flops(q, nx, ny, s, m):

@@ -321,6 +321,15 @@ hps_status hps_set_blocking(hps_plan *plan, hps_prec prec, int nb_panel);
  * (enable = 1, the default) or report them with info = -kmax (enable = 0). */
 hps_status hps_set_fp64_fallback(hps_plan *plan, int enable);
 
+/* Mixed path: how refinement decides after the FIRST correction.
+ * residual = 1 (default): on the true residuals, estimating X_1's error per
+ * column as eta_1 r_1 / r_0 (see hps_condense); residual = 0: on the
+ * correction alone, eta_1^2 (one residual fewer to reduce; it reads the
+ * error several times low after one correction, so use it only with a
+ * tolerance well below the accuracy wanted).  From the second correction
+ * on both use eta_k^2 / eta_{k-1}.  HPS_ERR_ARG for other values. */
+hps_status hps_set_refine_stop(hps_plan *plan, int residual);
+
 /* Number of leaves the last HPS_MIXED_FP32 hps_condense call re-condensed in
  * FP64; waits for the stream of that call. */
 hps_status hps_fallback_count(hps_plan *plan, int *count);

@@ -359,7 +359,7 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                          const float *__restrict__ Dh, const float *__restrict__ Dl,
                          const float *__restrict__ nf, float *__restrict__ Xs, float2 *__restrict__ Dp,
                          int cw_max, const double *__restrict__ ub = nullptr, bool sep = false,
-                         unsigned *__restrict__ rmax = nullptr) {
+                         unsigned *__restrict__ rmax = nullptr, float *__restrict__ rl = nullptr) {
     constexpr int G = 4;
     const int p = L.p, q = L.q, r = L.r, nbd = L.nbd, n = L.n, p2 = p * p;
     for (int e = threadIdx.x; e < 2 * p2; e += NT) Dp[e] = make_float2(Dh[e], Dl[e]);
@@ -429,8 +429,13 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
         }
         // each thread's column group is the same in every pass of this
         // loop (NT is a multiple of ng), so its column maxima of |R| are
-        // kept in registers and folded into rmax once per chunk
-        float rloc[G] = {0.0f, 0.0f, 0.0f, 0.0f};
+        // kept in its own shared-memory slots rl[t * NT + tid] (not in
+        // registers, which the kernel has none to spare) and folded into
+        // rmax once per chunk
+        if (rmax) {
+#pragma unroll
+            for (int t = 0; t < G; ++t) rl[t * NT + threadIdx.x] = 0.0f;
+        }
         for (int w = threadIdx.x; w < n * ng; w += NT) {
             const int rr = w / ng, g = w - rr * ng;
             const int i = rr / q + 1, j = rr - (i - 1) * q + 1, node = i * p + j;
@@ -560,7 +565,7 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                 }
                 const float rv = __fadd_rn(au.hi, au.lo);
                 M[(long long)rr * L.LDC + L.n4 + c] = (T)rv;
-                rloc[t] = fmaxf(rloc[t], fabsf(rv));
+                if (rmax) rl[t * NT + threadIdx.x] = fmaxf(rl[t * NT + threadIdx.x], fabsf(rv));
             }
         }
         if (rmax && threadIdx.x < n * ng) {
@@ -568,8 +573,9 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
 #pragma unroll
             for (int t = 0; t < G; ++t) {
                 const int cc = g * G + t;
+                const float v = rl[t * NT + threadIdx.x];
                 if (cc < cw)   // non-negative floats order like their bit patterns; NaN maps high
-                    atomicMax(&rmax[c0 + cc], rloc[t] == rloc[t] ? __float_as_uint(rloc[t]) : 0x7f800000u);
+                    atomicMax(&rmax[c0 + cc], v == v ? __float_as_uint(v) : 0x7f800000u);
             }
         }
         __syncthreads();
@@ -892,20 +898,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
                 while (!done && it < P.kmax) {
                     float *xs = (float *)((float2 *)sm.Ps + 2 * L.p * L.p);
                     // the first two residuals also record their column maxima
-                    unsigned *rm = it == 0 ? rn0 : it == 1 ? rn1 : nullptr;
-                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl, sep, rm);
-                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, sep, rm);
-                    else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, false, rm);
+                    unsigned *rm = !P.residual_stop ? nullptr : it == 0 ? rn0 : it == 1 ? rn1 : nullptr;
+                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl, sep, rm, sm.rl);
+                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, sep, rm, sm.rl);
+                    else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, false, rm, sm.rl);
                     __syncthreads();
                     // after the first correction the true residual decides
                     // whether X_1 is already good enough
-                    if (it == 1 && residual_ratio_ok(rn1, rn0, eta, L.r, P.tol)) {
+                    if (it == 1 && P.residual_stop && residual_ratio_ok(rn1, rn0, eta, L.r, P.tol)) {
                         done = true;
                         break;
                     }
                     lu_solve<T, NB, 0, INV>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
                     // the correction-ratio estimate stops from the second correction on
-                    done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us, it >= 1 || P.kmax == 1);
+                    done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us,
+                                            it >= 1 || P.kmax == 1 || !P.residual_stop);
                     ++it;
                 }
                 if (!done) status = -it;

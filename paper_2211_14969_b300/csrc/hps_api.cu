@@ -126,6 +126,7 @@ struct hps_plan {
     int launches = 0;
     int forced_nb[2] = {0, 0};   // per path (FP64, mixed); 0 = automatic
     int fallback = 1;            // mixed path: re-condense non-converged leaves in FP64
+    int residual_stop = 1;       // mixed path: first correction's stop on the true residuals
     cudaStream_t last_stream = nullptr;
     // merge tree
     std::vector<Level> levels;
@@ -399,6 +400,7 @@ static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef,
     prm.kmax = kmax;
     prm.fallbacks = P->d_queue + 1;
     prm.fallback = P->fallback;
+    prm.residual_stop = P->residual_stop;
     prm.ub = d_ub;
     prm.u = d_u;
     cudaStream_t s = (cudaStream_t)stream;
@@ -658,6 +660,12 @@ hps_status hps_leaf_recover(hps_plan *P, const double *d_S, const double *d_W, i
 hps_status hps_set_fp64_fallback(hps_plan *P, int enable) {
     if (P == nullptr) return HPS_ERR_ARG;
     P->fallback = enable != 0;
+    return HPS_OK;
+}
+
+hps_status hps_set_refine_stop(hps_plan *P, int residual) {
+    if (P == nullptr || residual < 0 || residual > 1) return HPS_ERR_ARG;
+    P->residual_stop = residual;
     return HPS_OK;
 }
 

@@ -58,6 +58,7 @@ struct CondenseParams {
     double tol;
     int kmax;
     int fallback;          // mixed path: redo non-converged leaves in FP64
+    int residual_stop;     // mixed path: the first correction's stop on the true residuals (else eta_1^2)
     // leaf solve (hps_leaf_resolve): edge values per leaf [n_b][m] and the
     // solution at the nodes [p*p][m]; ub == nullptr condenses instead
     const double *ub;

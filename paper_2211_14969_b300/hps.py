@@ -64,6 +64,7 @@ def load_library():
     L.hps_set_timing.argtypes = [vp, i]
     L.hps_set_blocking.argtypes = [vp, i, i]
     L.hps_set_fp64_fallback.argtypes = [vp, i]
+    L.hps_set_refine_stop.argtypes = [vp, i]
     L.hps_set_merge_split.argtypes = [vp, i]
     L.hps_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.hps_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
@@ -75,7 +76,7 @@ def load_library():
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_condense_host", "hps_merge", "hps_solve",
                  "hps_merge_boxes", "hps_solve_boxes", "hps_slab_factor", "hps_slab_solve", "hps_iti_condense",
-                 "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split",
+                 "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split", "hps_set_refine_stop",
                  "hps_fallback_count",
                  "hps_phase_times", "hps_last_launch_count"):
         getattr(L, name).restype = i
@@ -227,6 +228,11 @@ class Plan:
     def set_fp64_fallback(self, on=True):
         """Mixed path: re-condense non-converged leaves in FP64 (default on)."""
         self.check(load_library().hps_set_fp64_fallback(self.handle, int(bool(on))), "hps_set_fp64_fallback")
+
+    def set_refine_stop(self, residual=True):
+        """Mixed path: stop after the first correction on the true residuals
+        (default) or on the correction ratio alone."""
+        self.check(load_library().hps_set_refine_stop(self.handle, int(bool(residual))), "hps_set_refine_stop")
 
     def set_merge_split(self, below=-1):
         """Levels with fewer than `below` merges solve over many CTAs (-1: SM count; 0: never)."""

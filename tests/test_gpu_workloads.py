@@ -97,3 +97,23 @@ def test_graph_replay_matches_direct_call(prec):
     torch.cuda.synchronize()
     for k in ("S", "T", "h", "W", "info"):
         assert torch.equal(out[k], ref[k]), k
+
+
+def test_autotune_orders_per_order_times(tmp_path):
+    """Per-order tuning on a mixed-order plan: every order present timed
+    for the candidate widths, cached per (p, prec, m), the fused plan set to
+    a width that fits every order, and the cache reused."""
+    w = WL.uneven(nx=16, ny=8, m=2)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    cache = str(tmp_path / "orders.json")
+    nb, per = tune.autotune_orders(plan, w.boxes(), w.kappa, coef, f, w.m, prec="fp32", cache_path=cache)
+    assert set(per) == set(int(p) for p in w.p)
+    assert all(nb in t for t in per.values())
+    import json
+    assert all(tune.order_key(p, "fp32", 2) in json.load(open(cache)) for p in per)
+    out = plan.condense(coef, f, m=w.m, prec="fp32", tol=1e-12, kmax=8)
+    torch.cuda.synchronize()
+    assert (out["info"].cpu().numpy() == 0).all()
+    nb2, per2 = tune.autotune_orders(plan, w.boxes(), w.kappa, coef, f, w.m, prec="fp32", cache_path=cache)
+    assert nb2 == nb and per2 == per
