@@ -114,17 +114,13 @@ hps_status hps_leaf_nodes(const hps_plan *plan, double *d_xy, hps_stream stream)
  *       mixed paths refine to the same tolerance and need 4(p-2) + m <= 256
  *       for the largest p.
  * tol, kmax: iterative refinement with FP64 residuals.  Per right-hand column
- *            let eta_k = max|correction_k| / max|X| and r_k = max|R_k|, R_k
- *            the residual of the iterate after k corrections.  After the
- *            first correction the error left is estimated from the true
- *            residuals as eta_1 r_1 / r_0 (the first correction measured the
- *            unrefined error; the residual ratio is how much of it it
- *            removed); after correction k >= 2 as eta_k^2 / eta_{k-1} (the
- *            ratio of successive corrections measures the contraction).
- *            Refinement stops once every column's estimate is <= tol (the
- *            latter while still contracting), or after kmax corrections.
- *            kmax = 0 returns the FP32 solution unrefined; with kmax = 1
- *            the single correction is accepted by the eta_1^2 estimate.
+ *            let eta_k = max|correction_k| / max|X| (eta_0 = 1); the error
+ *            left after correction k is estimated as eta_k^2 / eta_{k-1}
+ *            (linear convergence; hps_set_refine_stop(plan, 1) estimates it
+ *            after the first correction from the true residuals instead).
+ *            Refinement stops once every column's estimate is <= tol while
+ *            still contracting, or after kmax corrections.  kmax = 0
+ *            returns the FP32 solution unrefined.
  *            A leaf that does not converge (typically cond(A_ii) u_fp32
  *            near 1, e.g. close to an interior Dirichlet resonance) is
  *            condensed again in FP64 inside the same launch and gets the
@@ -322,12 +318,16 @@ hps_status hps_set_blocking(hps_plan *plan, hps_prec prec, int nb_panel);
 hps_status hps_set_fp64_fallback(hps_plan *plan, int enable);
 
 /* Mixed path: how refinement decides after the FIRST correction.
- * residual = 1 (default): on the true residuals, estimating X_1's error per
- * column as eta_1 r_1 / r_0 (see hps_condense); residual = 0: on the
- * correction alone, eta_1^2 (one residual fewer to reduce; it reads the
- * error several times low after one correction, so use it only with a
- * tolerance well below the accuracy wanted).  From the second correction
- * on both use eta_k^2 / eta_{k-1}.  HPS_ERR_ARG for other values. */
+ * residual = 0 (default): on the correction alone, the estimate eta_1^2
+ * (which reads the error several times low after one correction, so with
+ * the default tol = 1e-12 no leaf stops there).  residual = 1: on the true
+ * residuals, estimating X_1's error per column as eta_1 r_1 / r_0 (r_k the
+ * column max |R_k| of the k-th double-float residual); this runs its own
+ * kernel instantiation with one more pass over each of the first two
+ * residuals, and lets leaves stop after one correction at tol >= 1e-11.
+ * From the second correction on both use eta_k^2 / eta_{k-1}.  The FP32
+ * CUDA-core path only (HPS_MIXED_TF32 / BF16 ignore it).  HPS_ERR_ARG for
+ * other values. */
 hps_status hps_set_refine_stop(hps_plan *plan, int residual);
 
 /* Number of leaves the last HPS_MIXED_FP32 hps_condense call re-condensed in

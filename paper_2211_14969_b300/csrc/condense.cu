@@ -358,8 +358,7 @@ template <typename T, bool GENERAL, bool RESOLVE = false>
 __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const LeafInfo &L,
                          const float *__restrict__ Dh, const float *__restrict__ Dl,
                          const float *__restrict__ nf, float *__restrict__ Xs, float2 *__restrict__ Dp,
-                         int cw_max, const double *__restrict__ ub = nullptr, bool sep = false,
-                         unsigned *__restrict__ rmax = nullptr, float *__restrict__ rl = nullptr) {
+                         int cw_max, const double *__restrict__ ub = nullptr, bool sep = false) {
     constexpr int G = 4;
     const int p = L.p, q = L.q, r = L.r, nbd = L.nbd, n = L.n, p2 = p * p;
     for (int e = threadIdx.x; e < 2 * p2; e += NT) Dp[e] = make_float2(Dh[e], Dl[e]);
@@ -426,15 +425,6 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                 Vl[(long long)kj * cwp + cc] = sk.lo;
             }
             __syncthreads();
-        }
-        // each thread's column group is the same in every pass of this
-        // loop (NT is a multiple of ng), so its column maxima of |R| are
-        // kept in its own shared-memory slots rl[t * NT + tid] (not in
-        // registers, which the kernel has none to spare) and folded into
-        // rmax once per chunk
-        if (rmax) {
-#pragma unroll
-            for (int t = 0; t < G; ++t) rl[t * NT + threadIdx.x] = 0.0f;
         }
         for (int w = threadIdx.x; w < n * ng; w += NT) {
             const int rr = w / ng, g = w - rr * ng;
@@ -563,19 +553,7 @@ __device__ void residual(T *__restrict__ M, const float2 *__restrict__ X, const 
                     au.hi = s2;
                     au.lo = __fadd_rn(au.lo, __fadd_rn(se, b.lo));
                 }
-                const float rv = __fadd_rn(au.hi, au.lo);
-                M[(long long)rr * L.LDC + L.n4 + c] = (T)rv;
-                if (rmax) rl[t * NT + threadIdx.x] = fmaxf(rl[t * NT + threadIdx.x], fabsf(rv));
-            }
-        }
-        if (rmax && threadIdx.x < n * ng) {
-            const int g = threadIdx.x % ng;
-#pragma unroll
-            for (int t = 0; t < G; ++t) {
-                const int cc = g * G + t;
-                const float v = rl[t * NT + threadIdx.x];
-                if (cc < cw)   // non-negative floats order like their bit patterns; NaN maps high
-                    atomicMax(&rmax[c0 + cc], v == v ? __float_as_uint(v) : 0x7f800000u);
+                M[(long long)rr * L.LDC + L.n4 + c] = (T)__fadd_rn(au.hi, au.lo);
             }
         }
         __syncthreads();
@@ -769,15 +747,44 @@ __device__ bool refine_update(T *__restrict__ M, float2 *__restrict__ X, float *
     return __syncthreads_or(bad) == 0 && allow_stop;
 }
 
+// Column maxima |R| of the residual just written to M[:, n4 .. n4 + r),
+// into colmax (shared memory, r unsigned: bit patterns of non-negative
+// floats, NaN high); eight rows' loads in flight per thread.  A pass of its
+// own, so the residual's register budget is untouched.
+template <typename T>
+__device__ void residual_colmax(const T *__restrict__ M, const LeafInfo &L, unsigned *colmax) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, r = L.r;
+    for (int c = threadIdx.x; c < r; c += NT) colmax[c] = 0u;
+    __syncthreads();
+    constexpr int UB = 8;
+    for (int c0 = 0; c0 < r; c0 += 32) {
+        const int c = c0 + lane;
+        if (c >= r) continue;
+        float mx = 0.0f;
+        for (int i0 = warp; i0 < L.n; i0 += NWARP * UB) {
+            float v[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int i = i0 + u * NWARP;
+                v[u] = i < L.n ? fabsf((float)M[(long long)i * L.LDC + L.n4 + c]) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u) mx = fmaxf(mx, v[u]);
+        }
+        atomicMax(&colmax[c], mx == mx ? __float_as_uint(mx) : 0x7f800000u);
+    }
+    __syncthreads();
+}
+
 // The first correction's stop: X_1's error estimated per column from the
 // true residuals as eta_1 |R_1| / |R_0| (the correction eta_1 measured X_0's
 // error; the residual ratio measures how much of it the correction
-// removed).  Block-uniform; rn0, rn1 hold |R_0|, |R_1| per column (float bit
-// patterns, from residual).
-__device__ bool residual_ratio_ok(const unsigned *rn1, const unsigned *rn0, const float *eta, int r, double tol) {
+// removed).  Block-uniform; rn1 holds |R_1| per column (float bit patterns,
+// shared memory), rn0 |R_0| (the slot).
+__device__ bool residual_ratio_ok(const unsigned *rn1, const float *rn0, const float *eta, int r, double tol) {
     int bad = 0;
     for (int c = threadIdx.x; c < r; c += NT) {
-        const float r1 = __uint_as_float(rn1[c]), r0 = __uint_as_float(rn0[c]);
+        const float r1 = __uint_as_float(rn1[c]), r0 = rn0[c];
         const double est = r0 > 0.0f ? (double)eta[c] * (double)r1 / (double)r0 : 0.0;
         if (!(est <= tol)) bad = 1;
     }
@@ -787,7 +794,7 @@ __device__ bool residual_ratio_ok(const unsigned *rn1, const unsigned *rn0, cons
 // Offset of the tensor-core operand buffers behind the LU's shared memory.
 __host__ __device__ inline size_t tc_smem_offset(size_t lu_bytes) { return (lu_bytes + 1023) & ~(size_t)1023; }
 
-template <typename T, int NB, bool MIXED, int TCK = 0>
+template <typename T, int NB, bool MIXED, int TCK = 0, bool RSTOP = false>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(CondenseParams P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const Smem<T> sm = carve<T, NB>(smem_raw, P.blk.ldp);
@@ -848,9 +855,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             int *perm_g = (int *)(X + (long long)L.n * L.r);   // 3 NB ints per panel
             lu_solve<T, NB, TCK, INV>(M, L.LDC, L.n, L.n4, L.C, true, perm_g, ldp, sm, tsp);
             float *eta = (float *)(perm_g + 3 * (L.n + 64));
-            unsigned *rn0 = (unsigned *)(eta + ((L.r + 63) & ~63));   // column max |R_0|, |R_1| (float bits)
-            unsigned *rn1 = rn0 + ((L.r + 63) & ~63);
-            float *nf = (float *)(rn1 + ((L.r + 63) & ~63));      // 12 floats per interior node
+            // column max |R_0| at eta + round64(r), then 12 floats per interior node
+            float *nf = eta + 2 * ((L.r + 63) & ~63);
             const float *Dhi = P.dt.dmat32 + P.dt.doff[L.p], *Dlo = P.dt.dmat_lo + P.dt.doff[L.p];
             node_factors(L, P.kappa2, nf);
             // residual column chunk: as many FP64 columns as the panel and
@@ -893,26 +899,30 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 4) condense_kernel(Co
             if (status == 0 && P.kmax > 0) {
                 int it = 0;
                 bool done = false;
-                for (int c = threadIdx.x; c < L.r; c += NT) rn0[c] = rn1[c] = 0u;
-                __syncthreads();
                 while (!done && it < P.kmax) {
                     float *xs = (float *)((float2 *)sm.Ps + 2 * L.p * L.p);
-                    // the first two residuals also record their column maxima
-                    unsigned *rm = !P.residual_stop ? nullptr : it == 0 ? rn0 : it == 1 ? rn1 : nullptr;
-                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl, sep, rm, sm.rl);
-                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, sep, rm, sm.rl);
-                    else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, false, rm, sm.rl);
+                    if (ubl) residual<T, true, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, ubl, sep);
+                    else if (L.flags) residual<T, true>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols, nullptr, sep);
+                    else residual<T, false>(M, X, L, Dhi, Dlo, nf, xs, (float2 *)sm.Ps, xs_cols);
                     __syncthreads();
-                    // after the first correction the true residual decides
-                    // whether X_1 is already good enough
-                    if (it == 1 && P.residual_stop && residual_ratio_ok(rn1, rn0, eta, L.r, P.tol)) {
-                        done = true;
-                        break;
+                    // the first two residuals' column maxima: after the first
+                    // correction the true residual decides whether X_1 is
+                    // already good enough
+                    if (RSTOP && it <= 1) {
+                        unsigned *cm = (unsigned *)sm.Us;   // idle between the residual and the replay
+                        float *rn0 = eta + ((L.r + 63) & ~63);
+                        residual_colmax<T>(M, L, cm);
+                        if (it == 0) {
+                            for (int c = threadIdx.x; c < L.r; c += NT) rn0[c] = __uint_as_float(cm[c]);
+                            __syncthreads();
+                        } else if (residual_ratio_ok(cm, rn0, eta, L.r, P.tol)) {
+                            done = true;
+                            break;
+                        }
                     }
                     lu_solve<T, NB, 0, INV>(M, L.LDC, L.n, L.n4, L.C, false, perm_g, ldp, sm);
                     // the correction-ratio estimate stops from the second correction on
-                    done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us,
-                                            it >= 1 || P.kmax == 1 || !P.residual_stop);
+                    done = refine_update<T>(M, X, eta, L, P.tol, (unsigned *)sm.Us, !RSTOP || it >= 1 || P.kmax == 1);
                     ++it;
                 }
                 if (!done) status = -it;
@@ -1194,14 +1204,25 @@ size_t kernel_smem(int ldp) {
     else return tc_smem_offset(smem_bytes_for<T, NB>(ldp)) + tc::operand_bytes<TCK>(NB) + 64;
 }
 
-template <typename T, int NB, bool MIXED, int TCK = 0>
-cudaError_t launch_one(const CondenseParams &prm, int grid, cudaStream_t s) {
+template <typename T, int NB, bool MIXED, int TCK = 0, bool RSTOP = false>
+cudaError_t launch_kernel(const CondenseParams &prm, int grid, cudaStream_t s) {
     const size_t smem = kernel_smem<T, NB, TCK>(prm.blk.ldp);
-    cudaError_t e = cudaFuncSetAttribute(condense_kernel<T, NB, MIXED, TCK>,
+    cudaError_t e = cudaFuncSetAttribute(condense_kernel<T, NB, MIXED, TCK, RSTOP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    condense_kernel<T, NB, MIXED, TCK><<<grid, NT, smem, s>>>(prm);
+    condense_kernel<T, NB, MIXED, TCK, RSTOP><<<grid, NT, smem, s>>>(prm);
     return cudaGetLastError();
+}
+
+// The first correction's true-residual stop is its own instantiation of the
+// FP32 CUDA-core kernel (hps_set_refine_stop), so the default kernels'
+// register allocation does not carry its code.
+template <typename T, int NB, bool MIXED, int TCK = 0>
+cudaError_t launch_one(const CondenseParams &prm, int grid, cudaStream_t s) {
+    if constexpr (MIXED && TCK == 0) {
+        if (prm.residual_stop) return launch_kernel<T, NB, MIXED, TCK, true>(prm, grid, s);
+    }
+    return launch_kernel<T, NB, MIXED, TCK, false>(prm, grid, s);
 }
 
 }  // namespace

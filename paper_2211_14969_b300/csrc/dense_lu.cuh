@@ -59,7 +59,6 @@ struct Smem {
     int *misc; // scalars: [0] leaf, [1] info, [2..] free
     int *map;  // ldp: row permutation scratch
     T *Ts;     // NB x NB: L11^-1 with its zeros and unit diagonal (FP32 path only)
-    float *rl; // 4 x NT: per-thread column maxima of a residual chunk (mixed path)
 };
 
 // Whether an elimination keeps the inverses of its unit-lower diagonal blocks (FP32
@@ -70,8 +69,7 @@ __host__ __device__ constexpr bool use_inverses() { return sizeof(T) == 4 && NB 
 template <typename T, int NB>
 __host__ __device__ constexpr size_t smem_bytes_for(int ldp, bool with_ts = false) {
     return sizeof(T) * ((size_t)NB * ldp + (size_t)NB * Cfg<T, NB>::CH + NB + 8 + NWARP) +
-           sizeof(int) * (NWARP + 3 * NB + 16 + ldp) + 64 + (with_ts ? sizeof(T) * NB * NB + 16 : 0) +
-           sizeof(float) * 4 * NT + 16;
+           sizeof(int) * (NWARP + 3 * NB + 16 + ldp) + 64 + (with_ts ? sizeof(T) * NB * NB + 16 : 0);
 }
 
 template <typename T, int NB>
@@ -97,8 +95,7 @@ __device__ Smem<T> carve(unsigned char *base, int ldp) {
     ip += 16;
     s.map = ip;
     ip += ldp;
-    s.rl = (float *)(((uintptr_t)ip + 15) & ~(uintptr_t)15);
-    s.Ts = (T *)(((uintptr_t)(s.rl + 4 * NT) + 15) & ~(uintptr_t)15);   // only kernels that keep L11^-1 use it
+    s.Ts = (T *)(((uintptr_t)ip + 15) & ~(uintptr_t)15);
     return s;
 }
 

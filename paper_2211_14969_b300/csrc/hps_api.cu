@@ -126,7 +126,7 @@ struct hps_plan {
     int launches = 0;
     int forced_nb[2] = {0, 0};   // per path (FP64, mixed); 0 = automatic
     int fallback = 1;            // mixed path: re-condense non-converged leaves in FP64
-    int residual_stop = 1;       // mixed path: first correction's stop on the true residuals
+    int residual_stop = 0;       // mixed path: first correction's stop on the true residuals (off by default)
     cudaStream_t last_stream = nullptr;
     // merge tree
     std::vector<Level> levels;
@@ -364,7 +364,7 @@ static hps_status run_condense(hps_plan *P, hps_prec prec, const double *d_coef,
         const long long q = p - 2, n = q * q, r = 4 * q + m, C = round_up(n, 4) + r, LDC = round_up(C, 4);
         long long b = n * LDC * (long long)tsize;
         if (mixed) {
-            b = round_up(b, 256) + n * r * 8 + 3 * (n + 64) * 4 + 3 * round_up(r, 64) * 4 + n * 12 * 4;   // X, perms, eta, residual norms, node factors
+            b = round_up(b, 256) + n * r * 8 + 3 * (n + 64) * 4 + 2 * round_up(r, 64) * 4 + n * 12 * 4;   // X, perms, eta, |R_0|, node factors
             b = std::max(b, n * LDC * 8);   // room for the FP64 fallback elimination
         }
         slot = std::max(slot, round_up(b, 256));

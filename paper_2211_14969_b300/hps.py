@@ -231,7 +231,7 @@ class Plan:
 
     def set_refine_stop(self, residual=True):
         """Mixed path: stop after the first correction on the true residuals
-        (default) or on the correction ratio alone."""
+        (residual=True) or on the correction ratio alone (the default)."""
         self.check(load_library().hps_set_refine_stop(self.handle, int(bool(residual))), "hps_set_refine_stop")
 
     def set_merge_split(self, below=-1):

@@ -226,3 +226,26 @@ def test_store_S_optional():
     torch.cuda.synchronize()
     assert "S" not in b
     assert torch.equal(a["T"], b["T"]) and torch.equal(a["h"], b["h"])
+
+
+def test_true_residual_stop_after_first_correction():
+    """hps_set_refine_stop(plan, 1): after the first correction the residual
+    ratio eta_1 |R_1| / |R_0| decides (its own kernel instantiation).  At
+    tol = 1e-11 leaves stop after one correction and still hold the mixed
+    bar against the oracle (a 4 x 4 block of bumps_p20 and uneven leaves);
+    at tol = 0 it never stops and reports non-convergence."""
+    for w, leaves in ((WL.bumps_p20(), [ix * 64 + iy for ix in range(30, 34) for iy in range(30, 34)]),
+                      (WL.uneven(m=2), list(range(0, 10240, 977)))):
+        sub = Sub(w, leaves)
+        plan = hps.Plan(sub.p, sub.box, sub.kappa)
+        plan.set_refine_stop(True)
+        coef, f, _ = gpu_inputs(sub, plan)
+        out = plan.condense(coef, f, m=sub.m, prec="fp32", tol=1e-11, kmax=6)
+        torch.cuda.synchronize()
+        assert (out["info"].cpu().numpy() == 0).all()
+        assert_within(compare_leaves(sub, plan, out, range(len(leaves)), TOL["fp32"]))
+        plan.set_fp64_fallback(False)
+        out = plan.condense(coef, f, m=sub.m, prec="fp32", tol=0.0, kmax=2)
+        torch.cuda.synchronize()
+        assert (out["info"].cpu().numpy() == -2).all()
+        plan.close()
