@@ -49,7 +49,7 @@ REFINE_KMAX = 6
 # profiles/condense_kernel_bumps_p20.md (592-leaf case scaled by 4096/592),
 # keyed by the hash of the condensation kernel's sources it was taken on;
 # reported only while those sources still hash to that value.
-TRAFFIC_BY_SOURCE = {"595bbc05468d3add": {"fp32": 30.62e9, "fp64": 73.01e9}}
+TRAFFIC_BY_SOURCE = {"32bed28bed2e680f": {"fp32": 30.89e9, "fp64": 73.00e9}}
 CONDENSE_SOURCES = ("condense.cu", "dense_lu.cuh", "tc_gemm.cuh", "hps_internal.cuh")
 
 
