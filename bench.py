@@ -1098,9 +1098,11 @@ def run_merge_solve(args, rank, ws):
         pass
     res = {}
     u_ref = None
-    for name, below, steps, warmup in (("split", -1, args.steps, args.warmup),
-                                       ("one_cta_per_merge", 0, max(1, min(args.steps, 2)), 1)):
+    for name, below, tensor, steps, warmup in (("split", -1, True, args.steps, args.warmup),
+                                               ("split_parent_maps_fp64_pipe", -1, False, args.steps, args.warmup),
+                                               ("one_cta_per_merge", 0, True, max(1, min(args.steps, 2)), 1)):
         plan.set_merge_split(below)
+        plan.set_merge_tensor(tensor)
         with ClockSampler(uuid) as ck:
             t_merge = time_steps(lambda: plan.merge(w.nx, w.ny, out["T"], out["h"], m), steps, warmup, ws, stream)
         launches = plan.last_launch_count()
@@ -1115,6 +1117,7 @@ def run_merge_solve(args, rank, ws):
             row["u_relerr_vs_split"] = float((u - u_ref).norm() / u_ref.norm())
         res[name] = row
     plan.set_merge_split(-1)
+    plan.set_merge_tensor(True)
     slabs = {}
     for sw in (4, 8, 16):
         if sw <= w.nx:

@@ -252,6 +252,19 @@ hps_status hps_slab_factor(hps_plan *plan, int nx, int ny, int s, const double *
 hps_status hps_slab_solve(hps_plan *plan, const double *d_g, const double *d_S, const double *d_W, int m, double *d_u,
                           hps_stream stream);
 
+/* How hps_merge (and hps_merge_boxes, hps_slab_factor's slab merges) form
+ * the parents' maps [T | h] = gather + [Ta13; Tb23] [S3 | w3] (the merge of
+ * Section 2 above).  enable = 1 (default): levels whose shared edge has at
+ * least 128 nodes and whose parent boundary at least 256 run this product
+ * on the BF16 tensor cores, FP64-accurate: every row of [Ta13; Tb23] and
+ * every column of [S3 | w3] is scaled by a power of two and cut into eight
+ * 7-bit integer slices (exact in BF16); the 36 slice products with s + t
+ * below 8 accumulate exactly in FP32 over K-chunks of 128 and are summed in
+ * FP64 (error below 2^-53 relative to sum_k |a_ik| |b_kj|).  enable = 0:
+ * every level on the FP64 pipe.  A tensor-core wait that times out makes
+ * the merge return HPS_ERR_CUDA.  HPS_ERR_ARG for other values. */
+hps_status hps_set_merge_tensor(hps_plan *plan, int enable);
+
 /* How hps_merge solves Z [S3 | w3] = -[Ta31 Tb32 | ha3 + hb3] (the merge
  * of Section 2 above) on each level.  A level with fewer than `below`
  * merges runs a blocked LU with partial pivoting whose every step is spread
@@ -384,7 +397,8 @@ const char *hps_last_error(const hps_plan *plan);
 void hps_destroy(hps_plan *plan);
 
 /* ABI version: major * 100 + minor (1.01: hps_merge_boxes, hps_solve_boxes;
- * 1.02: hps_slab_factor, hps_slab_solve; 1.03: hps_iti_condense). */
+ * 1.02: hps_slab_factor, hps_slab_solve; 1.03: hps_iti_condense;
+ * 1.04: hps_set_merge_tensor). */
 int hps_version(void);
 
 #ifdef __cplusplus

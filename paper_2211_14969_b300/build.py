@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhps.so")
-SOURCES = ["hps_api.cu", "condense.cu", "merge.cu", "merge_split.cu", "noalloc.cu", "slab.cu"]
+SOURCES = ["hps_api.cu", "condense.cu", "merge.cu", "merge_split.cu", "noalloc.cu", "slab.cu", "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -43,7 +43,7 @@ struct DevBuf {
 
 struct Level {
     MergeLevelDev dev{};
-    DevBuf maps, aug, th, u, info, piv, u3;
+    DevBuf maps, aug, th, u, info, piv, u3, oz;
 };
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
@@ -139,6 +139,8 @@ struct hps_plan {
     int slab_nx = 0, slab_ny = 0, slab_s = 0, slab_m = -1;
     bool slabbed = false;
     int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
+    int merge_tensor = 1;  // parents' [T | h] of large levels on the tensor cores (ozaki.cu)
+    DevBuf oz_err;         // their timeout flag
     SplitAux split_aux{nullptr, nullptr, nullptr};   // look-ahead stream and events, made on first use
     // hps_condense_host: device copies of the inputs and outputs, the chunk
     // work-queue orders and counters, two more streams and their events
@@ -182,7 +184,7 @@ struct hps_plan {
 
 extern "C" {
 
-int hps_version(void) { return 103; }
+int hps_version(void) { return 104; }
 
 const char *hps_last_error(const hps_plan *plan) {
     if (plan == nullptr) return g_build_error.c_str();
@@ -802,7 +804,7 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
     cudaStream_t s = (cudaStream_t)stream;
     for (auto &L : P->levels) {
         L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
-        L.piv.release(); L.u3.release();
+        L.piv.release(); L.u3.release(); L.oz.release();
     }
     P->levels.clear();
     P->merged = false;
@@ -826,6 +828,11 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
     P->levels.resize(hl.size());
     cudaError_t e = cudaSuccess;
     const int nbc0 = 2 * (wx0 + wy0) * q;   // boundary nodes of a unit box
+    bool used_oz = false;
+    if (P->merge_tensor) {
+        if ((e = P->oz_err.ensure(sizeof(int))) != cudaSuccess) return P->cuda_fail(e, who);
+        if ((e = cudaMemsetAsync(P->oz_err.p, 0, sizeof(int), s)) != cudaSuccess) return P->cuda_fail(e, who);
+    }
     if (hl.empty() && d_root_Th) {
         // one unit box: the root is the box itself
         e = cudaMemcpy2DAsync(d_root_Th, (size_t)(nbc0 + m) * sizeof(double), d_T, (size_t)nbc0 * sizeof(double),
@@ -872,7 +879,20 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
             if ((e = cudaEventCreateWithFlags(&P->split_aux.a, cudaEventDisableTiming)) != cudaSuccess) break;
             if ((e = cudaEventCreateWithFlags(&P->split_aux.b, cudaEventDisableTiming)) != cudaSuccess) break;
         }
+        D.use_oz = 0;
+        if (form && P->merge_tensor && ozaki_applies(H.np, H.n3)) {
+            if ((e = L.oz.ensure(ozaki_scratch_bytes(H.nm, H.np, H.n3, m))) != cudaSuccess) break;
+            D.oz = ozaki_layout(L.oz.p, H.nm, H.np, H.n3, m, (int *)P->oz_err.p);
+            D.use_oz = 1;
+            used_oz = true;
+        }
         if ((e = launch_merge_level(D, form, s, split ? &P->split_aux : nullptr)) != cudaSuccess) break;
+    }
+    if (e == cudaSuccess && used_oz) {   // a tensor-core wait that timed out left its tile unwritten
+        int flag = 0;
+        e = cudaMemcpyAsync(&flag, P->oz_err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && flag) return P->fail(HPS_ERR_CUDA, std::string(who) + ": a tensor-core wait timed out");
     }
     if (e != cudaSuccess) return P->cuda_fail(e, who);
     if ((e = P->u_leaf.ensure((size_t)P->n_leaves * nbc0 * std::max(m, 1) * sizeof(double))) != cudaSuccess)
@@ -886,7 +906,7 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
     P->launches = 0;
     for (auto &L : P->levels) {
         const int steps = (L.dev.n3 + 15) / 16;
-        P->launches += 1 + (L.dev.Th ? 1 : 0) + (L.dev.ipiv ? 6 * steps - 3 : 1);
+        P->launches += 1 + (L.dev.Th ? (L.dev.use_oz ? 4 : 1) : 0) + (L.dev.ipiv ? 6 * steps - 3 : 1);
     }
     return HPS_OK;
 }
@@ -899,6 +919,12 @@ hps_status hps_merge(hps_plan *P, int nx, int ny, const double *d_T, const doubl
 hps_status hps_merge_boxes(hps_plan *P, int nx, int ny, int wx0, int wy0, const double *d_T, const double *d_h, int m,
                            double *d_root_Th, hps_stream stream) {
     return merge_tree(P, "hps_merge_boxes", nx, ny, wx0, wy0, d_T, d_h, m, d_root_Th, stream);
+}
+
+hps_status hps_set_merge_tensor(hps_plan *P, int enable) {
+    if (P == nullptr || enable < 0 || enable > 1) return HPS_ERR_ARG;
+    P->merge_tensor = enable;
+    return HPS_OK;
 }
 
 hps_status hps_set_merge_split(hps_plan *P, int below) {
@@ -1090,9 +1116,10 @@ void hps_destroy(hps_plan *P) {
     cudaDeviceSynchronize();
     for (auto &L : P->levels) {
         L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
-        L.piv.release(); L.u3.release();
+        L.piv.release(); L.u3.release(); L.oz.release();
     }
     P->u_leaf.release();
+    P->oz_err.release();
     P->slab_th.release(); P->slab_aug.release(); P->slab_piv.release(); P->slab_info.release(); P->slab_tmp.release();
     P->hstage.release();
     P->horder.release();

@@ -223,6 +223,7 @@ cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStr
         e = launch_dense_solve(L.aug, (long long)L.n3 * L.lda, L.n3, L.c3, C, L.lda, L.nm, L.info, s);
     if (e != cudaSuccess) return e;
     if (form_parent) {
+        if (L.use_oz) return launch_parent_ozaki(L, L.oz, s);
         const int ldt = L.np + L.m;
         dim3 grid((ldt + 31) / 32, (L.np + 31) / 32, L.nm);
         merge_parent<<<grid, NT, 0, s>>>(L);

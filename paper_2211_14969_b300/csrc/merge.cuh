@@ -1,11 +1,22 @@
 // Device-side description of one merge level (built on the host).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "hps_internal.cuh"
 
 namespace hps {
+
+// Scratch of the parents' [T | h] on the tensor cores (ozaki.cu): the
+// operands' integer slices (BF16, K padded to Kp, rows to Mp, columns to
+// Np) and their power-of-two scales per merge of the level.
+struct OzakiScratch {
+    __nv_bfloat16 *As, *Bs;   // [nm][8][Mp][Kp], [nm][8][Np][Kp]
+    int *Ea, *Fb;             // [nm][Mp], [nm][Np]
+    int Kp, Mp, Np;
+    int *err;                 // set when a tensor-core wait timed out
+};
 
 struct MergeLevelDev {
     int nm;    // merges at this level
@@ -26,6 +37,8 @@ struct MergeLevelDev {
     int *info;                       // [nm] zero-pivot step of Z (0 = none)
     int *ipiv;                       // [nm][n3] pivot rows: Z solved over many CTAs; null: one CTA per merge
     double *u3;                      // [nm][n3][m] shared-edge values of the downward pass
+    int use_oz;                      // form the parents' [T | h] on the tensor cores
+    OzakiScratch oz;
 };
 
 // A second stream and two events for the look-ahead of the split solve.
@@ -55,6 +68,14 @@ cudaError_t launch_gemv(const double *A, long long lda, int rows, int cols, cons
                         int ldy, int m, double alpha, double beta, const double *add, int ldadd, cudaStream_t s);
 cudaError_t launch_slab_bounds(int nslab, int n, int sq, int nxq, int m, const double *u, const double *g, double *ub,
                                cudaStream_t s);
+
+// The parents' [T | h] as an FP64-accurate product on the BF16 tensor cores
+// (ozaki.cu): for levels where ozaki_applies, with ozaki_scratch_bytes of
+// scratch laid out by ozaki_layout.
+bool ozaki_applies(int np, int n3);
+size_t ozaki_scratch_bytes(int nm, int np, int n3, int m);
+OzakiScratch ozaki_layout(void *base, int nm, int np, int n3, int m, int *err);
+cudaError_t launch_parent_ozaki(const MergeLevelDev &L, const OzakiScratch &Z, cudaStream_t s);
 
 cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s,
                                const SplitAux *aux = nullptr);

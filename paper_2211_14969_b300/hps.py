@@ -65,6 +65,7 @@ def load_library():
     L.hps_set_blocking.argtypes = [vp, i, i]
     L.hps_set_fp64_fallback.argtypes = [vp, i]
     L.hps_set_refine_stop.argtypes = [vp, i]
+    L.hps_set_merge_tensor.argtypes = [vp, i]
     L.hps_set_merge_split.argtypes = [vp, i]
     L.hps_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.hps_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
@@ -76,7 +77,7 @@ def load_library():
     L.hps_version.restype = i
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_condense_host", "hps_merge", "hps_solve",
                  "hps_merge_boxes", "hps_solve_boxes", "hps_slab_factor", "hps_slab_solve", "hps_iti_condense",
-                 "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split", "hps_set_refine_stop",
+                 "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split", "hps_set_refine_stop", "hps_set_merge_tensor",
                  "hps_fallback_count",
                  "hps_phase_times", "hps_last_launch_count"):
         getattr(L, name).restype = i
@@ -233,6 +234,11 @@ class Plan:
         """Mixed path: stop after the first correction on the true residuals
         (residual=True) or on the correction ratio alone (the default)."""
         self.check(load_library().hps_set_refine_stop(self.handle, int(bool(residual))), "hps_set_refine_stop")
+
+    def set_merge_tensor(self, on=True):
+        """Parents' maps of the large merge levels on the tensor cores
+        (FP64-accurate integer slices, default) or on the FP64 pipe."""
+        self.check(load_library().hps_set_merge_tensor(self.handle, int(bool(on))), "hps_set_merge_tensor")
 
     def set_merge_split(self, below=-1):
         """Levels with fewer than `below` merges solve over many CTAs (-1: SM count; 0: never)."""

@@ -241,3 +241,30 @@ def test_psi_curved_domain_pipeline(prec):
     assert rel(u_gpu[:, mask], u_ora[:, mask]) < (1e-12 if prec == "fp64" else 1e-10)
     exact = np.stack([w.dirichlet_data(*O.leaf_nodes(p, b)) for b in w.boxes()])
     assert rel(u_gpu[:, mask], exact[:, mask]) < 1e-9
+
+
+def test_parent_maps_on_tensor_cores_match_fp64_pipe():
+    """hps_set_merge_tensor: the parents' [T | h] of the levels with shared
+    edges of at least 128 nodes formed from integer slices on the BF16 tensor
+    cores against the same maps on the FP64 pipe (16 x 16 leaves of p = 20:
+    the two top levels, shared edges of 144 and 288 nodes), root map and
+    solution; and the tensor-core merge's solution against the oracle."""
+    w = WL.bumps(p=20, nx=16, ny=16, kappa=60.0, seed=4, m=1)
+    w.dirichlet = "planewave"
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    out = plan.condense(coef, f, m=1)
+    keys = O.outer_boundary_keys(20, 16, 16)
+    g = torch.from_numpy(np.array([w.dirichlet_data(*O.key_coords(20, k, 16, 16)) for k in keys])).cuda()
+    res = {}
+    for on in (False, True):
+        plan.set_merge_tensor(on)
+        th = plan.merge_boxes(16, 16, 1, 1, out["T"], out["h"], 1, root=True)
+        plan.merge(16, 16, out["T"], out["h"], 1)
+        u = plan.solve(g, out["S"], out["W"], 1)
+        torch.cuda.synchronize()
+        res[on] = (th.clone(), u.clone())
+    (th0, u0), (th1, u1) = res[False], res[True]
+    assert float((th1 - th0).norm() / th0.norm()) < 1e-13
+    assert float((u1 - u0).norm() / u0.norm()) < 1e-12
+    plan.close()
