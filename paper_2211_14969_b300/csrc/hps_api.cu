@@ -141,6 +141,7 @@ struct hps_plan {
     int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
     int merge_tensor = 1;  // parents' [T | h] of large levels on the tensor cores (ozaki.cu)
     DevBuf oz_err;         // their timeout flag
+    DevBuf slab_oz;        // tensor-core scratch of SlabLU's interface solves
     SplitAux split_aux{nullptr, nullptr, nullptr};   // look-ahead stream and events, made on first use
     // hps_condense_host: device copies of the inputs and outputs, the chunk
     // work-queue orders and counters, two more streams and their events
@@ -879,11 +880,14 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
             if ((e = cudaEventCreateWithFlags(&P->split_aux.a, cudaEventDisableTiming)) != cudaSuccess) break;
             if ((e = cudaEventCreateWithFlags(&P->split_aux.b, cudaEventDisableTiming)) != cudaSuccess) break;
         }
-        D.use_oz = 0;
-        if (form && P->merge_tensor && ozaki_applies(H.np, H.n3)) {
-            if ((e = L.oz.ensure(ozaki_scratch_bytes(H.nm, H.np, H.n3, m))) != cudaSuccess) break;
-            D.oz = ozaki_layout(L.oz.p, H.nm, H.np, H.n3, m, (int *)P->oz_err.p);
-            D.use_oz = 1;
+        D.use_oz = form && P->merge_tensor && ozaki_applies(H.np, H.n3);
+        D.oz_solve = split && P->merge_tensor && split_solve_blocked(H.n3, H.np + m);
+        if (D.use_oz || D.oz_solve) {
+            size_t bytes = 0;
+            if (D.use_oz) bytes = ozaki_scratch_bytes(H.nm, H.np, H.n3, H.np + m);
+            if (D.oz_solve) bytes = std::max(bytes, split_solve_scratch(H.nm, H.n3, H.np + m));
+            if ((e = L.oz.ensure(bytes)) != cudaSuccess) break;
+            D.oz = ozaki_layout(L.oz.p, H.nm, H.np, H.n3, H.np + m, (int *)P->oz_err.p);
             used_oz = true;
         }
         if ((e = launch_merge_level(D, form, s, split ? &P->split_aux : nullptr)) != cudaSuccess) break;
@@ -905,8 +909,8 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
     P->merged = true;
     P->launches = 0;
     for (auto &L : P->levels) {
-        const int steps = (L.dev.n3 + 15) / 16;
-        P->launches += 1 + (L.dev.Th ? (L.dev.use_oz ? 4 : 1) : 0) + (L.dev.ipiv ? 6 * steps - 3 : 1);
+        P->launches += 1 + (L.dev.Th ? (L.dev.use_oz ? 4 : 1) : 0) +
+                       (L.dev.ipiv ? split_solve_launches(L.dev.n3, L.dev.np + L.dev.m, L.dev.oz_solve != 0, true) : 1);
     }
     return HPS_OK;
 }
@@ -1030,6 +1034,15 @@ hps_status hps_slab_factor(hps_plan *P, int nx, int ny, int s, const double *d_T
         }
         double *aug = (double *)P->slab_aug.p;
         const double *th = (const double *)P->slab_th.p;
+        const bool blocked = split && P->merge_tensor && split_solve_blocked(n, 2 * n + m);
+        OzakiScratch oz{};
+        if (blocked) {
+            if ((e = P->slab_oz.ensure(split_solve_scratch(1, n, 2 * n + m))) != cudaSuccess ||
+                (e = P->oz_err.ensure(sizeof(int))) != cudaSuccess ||
+                (e = cudaMemsetAsync(P->oz_err.p, 0, sizeof(int), st)) != cudaSuccess)
+                return P->cuda_fail(e, "hps_slab_factor: tensor-core scratch");
+            oz = ozaki_layout(P->slab_oz.p, 1, n, n, 2 * n + m, (int *)P->oz_err.p);
+        }
         for (int k = 0; k < S - 1 && e == cudaSuccess; ++k) {
             SlabStepDev D{};
             D.n = n; D.m = m; D.ldt = ldt; D.np = nps; D.lda = lda; D.c3 = c3; D.last = k == S - 2;
@@ -1043,9 +1056,17 @@ hps_status hps_slab_factor(hps_plan *P, int nx, int ny, int s, const double *d_T
             L.aug = D.aug;
             L.info = (int *)P->slab_info.p + k;
             L.ipiv = (int *)P->slab_piv.p + (size_t)k * n;
+            L.oz_solve = blocked;
+            L.oz = oz;
             e = split ? launch_split_solve(L, L.ipiv, st, &P->split_aux)
                       : launch_dense_solve(D.aug, 0, n, c3, c3 + 2 * n + m, lda, 1, L.info, st);
-            launches += 2 + (split ? 6 * ((n + 15) / 16) - 3 : 1);
+            launches += 2 + (split ? split_solve_launches(n, 2 * n + m, blocked, true) : 1);
+        }
+        if (e == cudaSuccess && blocked) {   // a tensor-core wait that timed out left its tile unwritten
+            int flag = 0;
+            e = cudaMemcpyAsync(&flag, P->oz_err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess && flag) return P->fail(HPS_ERR_CUDA, "hps_slab_factor: a tensor-core wait timed out");
         }
         if (e != cudaSuccess) return P->cuda_fail(e, "hps_slab_factor: interface block LU");
     }
@@ -1120,6 +1141,7 @@ void hps_destroy(hps_plan *P) {
     }
     P->u_leaf.release();
     P->oz_err.release();
+    P->slab_oz.release();
     P->slab_th.release(); P->slab_aug.release(); P->slab_piv.release(); P->slab_info.release(); P->slab_tmp.release();
     P->hstage.release();
     P->horder.release();

@@ -38,7 +38,8 @@ struct MergeLevelDev {
     int *ipiv;                       // [nm][n3] pivot rows: Z solved over many CTAs; null: one CTA per merge
     double *u3;                      // [nm][n3][m] shared-edge values of the downward pass
     int use_oz;                      // form the parents' [T | h] on the tensor cores
-    OzakiScratch oz;
+    int oz_solve;                    // split solve: right-hand side in blocks, tensor-core updates
+    OzakiScratch oz;                 // scratch of both (the larger of the two jobs)
 };
 
 // A second stream and two events for the look-ahead of the split solve.
@@ -69,12 +70,37 @@ cudaError_t launch_gemv(const double *A, long long lda, int rows, int cols, cons
 cudaError_t launch_slab_bounds(int nslab, int n, int sq, int nxq, int m, const double *u, const double *g, double *ub,
                                cudaStream_t s);
 
-// The parents' [T | h] as an FP64-accurate product on the BF16 tensor cores
-// (ozaki.cu): for levels where ozaki_applies, with ozaki_scratch_bytes of
-// scratch laid out by ozaki_layout.
+// One FP64-accurate product on the BF16 tensor cores (ozaki.cu) for nm
+// independent problems s, A_s (M x K) times B_s (K x N):
+//   gather: row P of A_s is the children's row of parent node P at the
+//           shared-edge columns (merge level L), else a[s sa + P lda + k];
+//   B_s[k][c] = b[s sb + k ldb + c];
+//   form:   the merge's parent map, C_s = G_s + A_s B_s with G the gathered
+//           diag(Ta11, Tb22) | [ha1; hb2]; else C_s -= A_s B_s in place;
+//   C_s[P][c] = c[s sc + P ldc + c].
+struct OzJob {
+    int nm, M, K, N;
+    int gather;
+    const double *a;
+    long long sa;
+    int lda;
+    const double *b;
+    long long sb;
+    int ldb;
+    int form;
+    double *c;
+    long long sc;
+    int ldc;
+    MergeLevelDev L;
+};
+
+// Scratch of ozaki_scratch_bytes(nm, M, K, N) holds the slices of any job
+// up to those sizes; ozaki_layout lays it out (launch_ozaki does so per job).
 bool ozaki_applies(int np, int n3);
-size_t ozaki_scratch_bytes(int nm, int np, int n3, int m);
-OzakiScratch ozaki_layout(void *base, int nm, int np, int n3, int m, int *err);
+size_t ozaki_scratch_bytes(int nm, int M, int K, int N);
+OzakiScratch ozaki_layout(void *base, int nm, int M, int K, int N, int *err);
+cudaError_t launch_ozaki(const OzJob &J, const OzakiScratch &Z, cudaStream_t s);
+// the parents' [T | h] of a merge level
 cudaError_t launch_parent_ozaki(const MergeLevelDev &L, const OzakiScratch &Z, cudaStream_t s);
 
 cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStream_t s,
@@ -85,6 +111,12 @@ cudaError_t launch_merge_level(const MergeLevelDev &L, bool form_parent, cudaStr
 // shared memory (split_solve_fits).
 cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s, const SplitAux *aux = nullptr);
 bool split_solve_fits(int n3);
+// With L.oz_solve (where split_solve_blocked holds) the right-hand side is
+// eliminated in blocks with tensor-core updates (split_solve_scratch bytes
+// of Ozaki scratch); split_solve_launches counts the kernels either way.
+bool split_solve_blocked(int n3, int nrhs);
+size_t split_solve_scratch(int nm, int n3, int nrhs);
+int split_solve_launches(int n3, int nrhs, bool blocked, bool aux);
 cudaError_t launch_merge_down(const MergeLevelDev &L, const double *upar, double *uchild, cudaStream_t s);
 cudaError_t launch_leaf_recover(int n_leaves, int p, int m, const double *S, const double *W,
                                 const double *ub, double *u, cudaStream_t s);

@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(PNT) split_panel(double *__restrict__ aug, lon
 // Interchanges and the unit-lower solve for the columns right of the panel.
 template <int NB>
 __global__ void __launch_bounds__(CNT) split_swap_lower(double *__restrict__ aug, long long stride, int n3, int lda,
-                                                        int k, int nbk, int C, const int *__restrict__ ipiv) {
+                                                        int k, int nbk, int c0, int C, const int *__restrict__ ipiv,
+                                                        int swap) {
     __shared__ double L[NB][NB];
     __shared__ int pv[NB];
     const int s = blockIdx.y;
@@ -128,12 +129,12 @@ __global__ void __launch_bounds__(CNT) split_swap_lower(double *__restrict__ aug
     }
     if (threadIdx.x < NB) pv[threadIdx.x] = threadIdx.x < nbk ? ipiv[(long long)s * n3 + k + threadIdx.x] : 0;
     __syncthreads();
-    const int col = k + nbk + blockIdx.x * CNT + threadIdx.x;
+    const int col = c0 + blockIdx.x * CNT + threadIdx.x;
     if (col >= C) return;
     double x[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        if (j < nbk) {
+        if (swap && j < nbk) {
             const int r = pv[j];
             double *a = A + (long long)(k + j) * lda + col;
             if (r != k + j) {
@@ -158,6 +159,26 @@ __global__ void __launch_bounds__(CNT) split_swap_lower(double *__restrict__ aug
 #pragma unroll
     for (int j = 0; j < NB; ++j)
         if (j < nbk) A[(long long)(k + j) * lda + col] = x[j];
+}
+
+// The interchanges of pivot steps k..k+np-1, in order, for the columns
+// [c0, c1): a block's L columns left of its panel, or the right-hand side
+// once per elimination block.
+__global__ void __launch_bounds__(CNT) split_swap_cols(double *__restrict__ aug, long long stride, int n3, int lda,
+                                                       int k, int np, int c0, int c1, const int *__restrict__ ipiv) {
+    const int s = blockIdx.y;
+    const int col = c0 + blockIdx.x * CNT + threadIdx.x;
+    if (col >= c1) return;
+    double *A = aug + (long long)s * stride + col;
+    const int *pv = ipiv + (long long)s * n3 + k;
+    for (int j = 0; j < np; ++j) {
+        const int r = pv[j];
+        if (r != k + j) {
+            const double t = A[(long long)(k + j) * lda];
+            A[(long long)(k + j) * lda] = A[(long long)r * lda];
+            A[(long long)r * lda] = t;
+        }
+    }
 }
 
 // X1 = U11^{-1} Y1 for the right-hand columns of block row kb.
@@ -280,8 +301,40 @@ __global__ void __launch_bounds__(256) split_gemm_n16(double *__restrict__ aug, 
 }  // namespace
 
 constexpr int kSplitNB = 16;
+constexpr int kSplitKB = 128;   // elimination block of the right-hand side with oz_solve (a multiple of kSplitNB)
 
 bool split_solve_fits(int n3) { return (size_t)((n3 | 1) * kSplitNB) * sizeof(double) <= 200 * 1024; }
+
+bool split_solve_blocked(int n3, int nrhs) { return n3 >= 2 * kSplitKB && n3 <= 8192 && nrhs >= kSplitKB; }
+
+size_t split_solve_scratch(int nm, int n3, int nrhs) { return ozaki_scratch_bytes(nm, n3, kSplitKB, nrhs); }
+
+// the kernels launch_split_solve issues (an Ozaki job is four)
+int split_solve_launches(int n3, int nrhs, bool blocked, bool aux) {
+    constexpr int NB = kSplitNB;
+    const int CZ = blocked ? n3 : n3 + nrhs;   // columns past the panel the LU steps touch, counted from 0
+    int n = 0, kb0 = 0;
+    for (int k = 0; k < n3; k += NB) {
+        const int nbk = n3 - k < NB ? n3 - k : NB;
+        const int cr = CZ - (k + nbk), nr = n3 - (k + nbk);
+        n += 1 + (cr > 0) + (blocked && k > kb0);
+        if (nr > 0 && cr > 0) n += (aux && cr > (nr < NB ? nr : NB)) ? 2 : 1;
+        const int kb1 = k + nbk;
+        if (blocked && (kb1 - kb0 == kSplitKB || kb1 == n3)) {
+            n += 1;
+            for (int j = kb0; j < kb1; j += NB) n += 1 + (j + NB < kb1);
+            if (kb1 < n3) n += 4;
+            kb0 = kb1;
+        }
+    }
+    if (!blocked) return n + 2 * ((n3 + NB - 1) / NB) - 1;
+    for (int b0 = ((n3 - 1) / kSplitKB) * kSplitKB; b0 >= 0; b0 -= kSplitKB) {
+        const int b1 = b0 + kSplitKB < n3 ? b0 + kSplitKB : n3;
+        for (int kb = ((b1 - 1) / NB) * NB; kb >= b0; kb -= NB) n += 1 + (kb > b0);
+        if (b0 > 0) n += 4;
+    }
+    return n;
+}
 
 cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t st, const SplitAux *aux) {
     constexpr int NB = kSplitNB;
@@ -297,19 +350,49 @@ cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s
         split_gemm<NB><<<dim3((nc + GT - 1) / GT, (nr + GT - 1) / GT, nm), 256, 0, s>>>(L.aug, stride, lda, r0, nr, c0,
                                                                                         nc, ka, kb, K);
     };
+    const int nrhs = C - L.c3;
+    // With oz_solve the LU steps eliminate only Z's columns; the right-hand
+    // side is eliminated per block of kSplitKB rows (interchanges, the
+    // block's unit-lower solve, then one tensor-core update of every row
+    // below it), as in a blocked LU solve.
+    const bool blocked = L.oz_solve != 0;
+    const int CZ = blocked ? n3 : C;   // last column the LU steps touch
+    auto rhs_update = [&](int r0, int M, int k0, int K) -> cudaError_t {
+        OzJob J{};
+        J.nm = nm;
+        J.M = M;
+        J.K = K;
+        J.N = nrhs;
+        J.a = L.aug + (long long)r0 * lda + k0;
+        J.sa = stride;
+        J.lda = lda;
+        J.b = L.aug + (long long)k0 * lda + L.c3;
+        J.sb = stride;
+        J.ldb = lda;
+        J.c = L.aug + (long long)r0 * lda + L.c3;
+        J.sc = stride;
+        J.ldc = lda;
+        return launch_ozaki(J, L.oz, st);
+    };
     // With aux, look-ahead: each step first updates only the next panel's
     // columns, and the rest of its trailing update runs on the side stream
     // while the next panel is factored (the two touch disjoint columns); the
     // next step's interchanges wait for it.
     bool pending = false;
+    int kb0 = 0;   // first row of the current elimination block
     for (int k = 0; k < n3; k += NB) {
         const int nbk = n3 - k < NB ? n3 - k : NB;
         const size_t sm = (size_t)(((n3 - k) | 1) * NB) * sizeof(double);
         split_panel<NB><<<nm, PNT, sm, st>>>(L.aug, stride, n3, lda, k, nbk, ipiv, L.info);
         if (pending && (e = cudaStreamWaitEvent(st, aux->b, 0)) != cudaSuccess) return e;
         pending = false;
-        const int cr = C - (k + nbk);
-        if (cr > 0) split_swap_lower<NB><<<dim3((cr + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, k, nbk, C, ipiv);
+        const int cr = CZ - (k + nbk);
+        if (cr > 0)
+            split_swap_lower<NB><<<dim3((cr + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, k, nbk, k + nbk,
+                                                                                 CZ, ipiv, 1);
+        if (blocked && k > kb0)
+            split_swap_cols<<<dim3((k - kb0 + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, k, nbk, kb0, k,
+                                                                                 ipiv);
         const int nr = n3 - (k + nbk);
         if (nr > 0 && cr > 0) {
             const int next_w = nr < NB ? nr : NB;
@@ -326,15 +409,45 @@ cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s
             }
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int kb1 = k + nbk;
+        if (blocked && (kb1 - kb0 == kSplitKB || kb1 == n3)) {
+            // the right-hand side of block rows [kb0, kb1): its interchanges in
+            // order, the unit-lower solve inside the block, the rows below
+            split_swap_cols<<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, kb0, kb1 - kb0,
+                                                                              L.c3, C, ipiv);
+            for (int j = kb0; j < kb1; j += NB) {
+                const int w = kb1 - j < NB ? kb1 - j : NB;
+                split_swap_lower<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, j, w,
+                                                                                       L.c3, C, ipiv, 0);
+                if (j + w < kb1) gemm(st, j + w, kb1 - (j + w), L.c3, nrhs, j, j, w);
+            }
+            if (kb1 < n3 && (e = rhs_update(kb1, n3 - kb1, kb0, kb1 - kb0)) != cudaSuccess) return e;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            kb0 = kb1;
+        }
     }
     if (pending && (e = cudaStreamWaitEvent(st, aux->b, 0)) != cudaSuccess) return e;
-    const int nrhs = C - L.c3;
     const int last = ((n3 - 1) / NB) * NB;
-    for (int kb = last; kb >= 0; kb -= NB) {
-        const int nbk = n3 - kb < NB ? n3 - kb : NB;
-        split_upper<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, lda, kb, nbk, L.c3, C);
-        if (kb > 0) gemm(st, 0, kb, L.c3, nrhs, kb, kb, nbk);
+    if (!blocked) {
+        for (int kb = last; kb >= 0; kb -= NB) {
+            const int nbk = n3 - kb < NB ? n3 - kb : NB;
+            split_upper<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, lda, kb, nbk, L.c3, C);
+            if (kb > 0) gemm(st, 0, kb, L.c3, nrhs, kb, kb, nbk);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    // back substitution per block from the bottom: inside the block, then
+    // one tensor-core update of every row above it
+    for (int b0 = ((n3 - 1) / kSplitKB) * kSplitKB; b0 >= 0; b0 -= kSplitKB) {
+        const int b1 = b0 + kSplitKB < n3 ? b0 + kSplitKB : n3;
+        for (int kb = ((b1 - 1) / NB) * NB; kb >= b0; kb -= NB) {
+            const int nbk = b1 - kb < NB ? b1 - kb : NB;
+            split_upper<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, lda, kb, nbk, L.c3, C);
+            if (kb > b0) gemm(st, b0, kb - b0, L.c3, nrhs, kb, kb, nbk);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (b0 > 0 && (e = rhs_update(0, b0, b0, b1 - b0)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

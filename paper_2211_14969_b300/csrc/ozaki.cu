@@ -41,7 +41,8 @@ namespace hps {
 namespace {
 
 constexpr int OZ_S = 8;       // slices per operand
-constexpr int OZ_KC = 64;     // K-chunk staged in shared memory
+constexpr int OZ_KC = 32;     // K-chunk staged in shared memory
+constexpr int OZ_KALIGN = 64; // K padding: a multiple of OZ_KC and of the B-slicing tile
 constexpr int OZ_TM = 128, OZ_TN = 64;
 constexpr int OZ_NT = 256;
 
@@ -115,26 +116,31 @@ __device__ __forceinline__ void oz_store8(const double *x, int e, __nv_bfloat16 
     }
 }
 
-// A slices: row P of A = the gathered child row (its shared-edge columns).
-// As[s][P][k] (rows padded to Mp, K to Kp with zeros), Ea[P]; a warp per
-// row, 8 consecutive k per lane.
-__global__ void __launch_bounds__(256) oz_slice_a(MergeLevelDev L, OzakiScratch Z) {
+// A slices: row P of A (a gathered child row, its shared-edge columns, or a
+// strided row).  As[s][P][k] (rows padded to Mp, K to Kp with zeros),
+// Ea[P]; a warp per row, 8 consecutive k per lane.
+__global__ void __launch_bounds__(256) oz_slice_a(OzJob J, OzakiScratch Z) {
     const int s = blockIdx.y;
     const int P = (blockIdx.x * 256 + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (P >= Z.Mp) return;
     const long long stride = (long long)Z.Mp * Z.Kp;
     __nv_bfloat16 *row = Z.As + (long long)s * OZ_S * stride + (long long)P * Z.Kp;
     const double *tr = nullptr;
-    const int *s3 = nullptr;
+    const int *s3 = nullptr;   // gathered rows: the row's entries at s3[k]
     int e = 0;
-    if (P < L.np) {
-        const ChildRef A = child_ref(L, L.ca[s]), B = child_ref(L, L.cb[s]);
-        const int chi = L.par_child[P];
-        const ChildRef &X = chi == 0 ? A : B;
-        s3 = chi == 0 ? L.s3a : L.s3b;
-        tr = X.T + (long long)L.par_idx[P] * X.ld;
+    if (P < J.M) {
+        if (J.gather) {
+            const MergeLevelDev &L = J.L;
+            const ChildRef A = child_ref(L, L.ca[s]), B = child_ref(L, L.cb[s]);
+            const int chi = L.par_child[P];
+            const ChildRef &X = chi == 0 ? A : B;
+            s3 = chi == 0 ? L.s3a : L.s3b;
+            tr = X.T + (long long)L.par_idx[P] * X.ld;
+        } else {
+            tr = J.a + (long long)s * J.sa + (long long)P * J.lda;
+        }
         double mx = 0.0;
-        for (int k = lane; k < L.n3; k += 32) mx = fmax(mx, fabs(tr[s3[k]]));
+        for (int k = lane; k < J.K; k += 32) mx = fmax(mx, fabs(tr[s3 ? s3[k] : k]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         e = oz_exp(mx);
@@ -144,36 +150,34 @@ __global__ void __launch_bounds__(256) oz_slice_a(MergeLevelDev L, OzakiScratch 
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int k = g * 8 + i;
-            x[i] = (tr && k < L.n3) ? tr[s3[k]] : 0.0;
+            x[i] = (tr && k < J.K) ? tr[s3 ? s3[k] : k] : 0.0;
         }
         oz_store8(x, e, row + g * 8, stride);
     }
     if (lane == 0) Z.Ea[(long long)s * Z.Mp + P] = e;
 }
 
-// B column exponents: column c of B = aug[:, c3 + c] over the n3 rows.
-__global__ void __launch_bounds__(256) oz_colexp_b(MergeLevelDev L, OzakiScratch Z) {
+// B column exponents over the K rows.
+__global__ void __launch_bounds__(256) oz_colexp_b(OzJob J, OzakiScratch Z) {
     const int s = blockIdx.y, c = blockIdx.x * 256 + threadIdx.x;
     if (c >= Z.Np) return;
-    const int N = L.np + L.m;
     double mx = 0.0;
-    if (c < N) {
-        const double *aug = L.aug + (long long)s * L.n3 * L.lda + L.c3 + c;
-        for (int k = 0; k < L.n3; ++k) mx = fmax(mx, fabs(aug[(long long)k * L.lda]));
+    if (c < J.N) {
+        const double *b = J.b + (long long)s * J.sb + c;
+        for (int k = 0; k < J.K; ++k) mx = fmax(mx, fabs(b[(long long)k * J.ldb]));
     }
     Z.Fb[(long long)s * Z.Np + c] = oz_exp(mx);
 }
 
 // B slices Bs[t][c][k] (K-contiguous) from a 64 (k) x 32 (c) shared tile;
 // a thread per (column, 8 consecutive k).
-__global__ void __launch_bounds__(256) oz_slice_b(MergeLevelDev L, OzakiScratch Z) {
+__global__ void __launch_bounds__(256) oz_slice_b(OzJob J, OzakiScratch Z) {
     __shared__ double tile[64][33];
     const int s = blockIdx.z, c0 = blockIdx.x * 32, k0 = blockIdx.y * 64;
-    const int N = L.np + L.m;
-    const double *aug = L.aug + (long long)s * L.n3 * L.lda + L.c3;
+    const double *b = J.b + (long long)s * J.sb;
     for (int e = threadIdx.x; e < 64 * 32; e += 256) {
         const int kk = e >> 5, cc = e & 31, k = k0 + kk, c = c0 + cc;
-        tile[kk][cc] = (k < L.n3 && c < N) ? aug[(long long)k * L.lda + c] : 0.0;
+        tile[kk][cc] = (k < J.K && c < J.N) ? b[(long long)k * J.ldb + c] : 0.0;
     }
     __syncthreads();
     const int cc = threadIdx.x >> 3, g = threadIdx.x & 7, c = c0 + cc;
@@ -203,30 +207,62 @@ __device__ __forceinline__ bool oz_wait(uint64_t *mbar, uint32_t phase) {
     return done != 0;
 }
 
-// Exactness periods of the FP32 accumulators, in K-chunks of OZ_KC = 64:
+// X 2^e rounded to nearest (ties to even), built from the bits of the
+// int64 X (|X| < 2^63) with integer operations; ldexp outside the normal
+// range.
+__device__ __forceinline__ double oz_scaled_i64(long long X, int e) {
+    if (X == 0) return 0.0;
+    const unsigned long long sg = X < 0 ? 1ull << 63 : 0ull;
+    unsigned long long u = X < 0 ? (unsigned long long)(-X) : (unsigned long long)X;
+    const int lz = __clzll((long long)u);
+    u <<= lz;                                   // leading one at bit 63
+    unsigned long long m = u >> 11;             // 53 significant bits
+    const unsigned long long rem = u & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) ++m;
+    int ex = 63 - lz + e;                       // X 2^e = (m / 2^52) 2^ex
+    if (m >> 53) { m >>= 1; ++ex; }
+    const int be = ex + 1023;
+    if (be <= 0 || be >= 2047) return ldexp((double)X, e);
+    return __longlong_as_double((long long)(sg | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// t 2^e for a float t that is zero or normal, by moving its exponent and
+// mantissa into a double (exact); ldexp outside the normal range.
+__device__ __forceinline__ double oz_scaled_f32(float t, int e) {
+    const unsigned b = __float_as_uint(t);
+    const int fe = (int)((b >> 23) & 0xFF);
+    if (fe == 0) return 0.0;
+    const int be = fe - 127 + e + 1023;
+    if (fe == 0xFF || be <= 0 || be >= 2047) return ldexp((double)t, e);
+    return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | ((unsigned long long)be << 52) |
+                                            ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
+// Exactness periods of the FP32 accumulators, in K-chunks of OZ_KC = 32:
 // D_d over K columns is a sum of at most (d + 1) K products of magnitude
 // <= 127^2, exact while (d + 1) K 127^2 < 2^24, i.e. K <= 1024, 512, 256,
 // 256, 128, 128 for d = 0..5.  D_6 and D_7 (weights 2^-56, 2^-63) stay in
 // tensor memory over the whole K: their FP32 rounding is below the FP64
 // product's own error bound.
 __device__ __forceinline__ int oz_period(int d) {
-    return d == 0 ? 16 : d == 1 ? 8 : d <= 3 ? 4 : d <= 5 ? 2 : 1 << 30;
+    return d == 0 ? 32 : d == 1 ? 16 : d <= 3 ? 8 : d <= 5 ? 4 : 1 << 30;
 }
+__device__ __forceinline__ bool oz_folds(int d, int c, int nc) { return (c + 1) % oz_period(d) == 0 || c == nc - 1; }
 
-// Th[P][c] = G[P][c] + 2^(Ea_P + Fb_c) (2^-49 X + 2^-56 (D_6 + 2^-7 D_7)),
-// X = sum_{d <= 5} D_d 2^(7 (5 - d)) in exact int64 fixed point.
-// Stages j = 8 ci + sl: A slice sl of K-chunk ci against the chunk's B
-// slices t <= 7 - sl; A and B double-buffered, the next stage's loads in
-// flight during the current stage's MMAs.
-__global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(MergeLevelDev L, OzakiScratch Z) {
+// (A B)[P][c] = 2^(Ea_P + Fb_c) (2^-49 X + 2^-56 (D_6 + 2^-7 D_7)),
+// X = sum_{d <= 5} D_d 2^(7 (5 - d)) in exact int64 fixed point; the
+// epilogue writes the merge's Th = G + A B or updates C -= A B in place.
+// Chunk c: the 36 products of its eight A and eight B slices (72 MMAs of
+// K = 16), from buffer c & 1; chunk c + 1's loads are issued once chunk
+// c - 1's MMAs are done, and chunk c + 1's MMAs queue behind chunk c's,
+// except after a chunk whose accumulators are folded.
+__global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
     extern __shared__ __align__(1024) unsigned char smem[];
     using namespace tc;
     constexpr int BSL = OZ_TN * OZ_KC * 2;           // one B slice tile, bytes
-    constexpr int BCH = OZ_S * BSL;                  // one chunk's B slices
     constexpr int ASL = OZ_TM * OZ_KC * 2;           // one A slice tile
-    unsigned char *bs = smem;                        // [2][OZ_S] B slice tiles
-    unsigned char *as = smem + 2 * BCH;              // [2] A slice tiles
-    uint64_t *mbar = (uint64_t *)(as + 2 * ASL);     // [2] MMA completion, one per A buffer
+    constexpr int BUF = OZ_S * (ASL + BSL);          // one chunk: 8 A + 8 B slices
+    uint64_t *mbar = (uint64_t *)(smem + 2 * BUF);   // [2] MMA completion, one per buffer
     uint32_t *tmem_p = (uint32_t *)(mbar + 2);
     const int s = blockIdx.z, tm = blockIdx.y * OZ_TM, tn = blockIdx.x * OZ_TN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -249,149 +285,205 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(MergeLevelDev L, OzakiScratc
     const long long sa = (long long)Z.Mp * Z.Kp, sb = (long long)Z.Np * Z.Kp;
     const __nv_bfloat16 *Ag = Z.As + (long long)s * OZ_S * sa;
     const __nv_bfloat16 *Bg = Z.Bs + (long long)s * OZ_S * sb;
-    const int nc = Z.Kp / OZ_KC, NS = nc * OZ_S;
-    // cp.async of stage j's A slice (and, at sl = 0, its chunk's B slices)
-    auto load_stage = [&](int j) {
-        const int ci = j / OZ_S, sl = j % OZ_S, kc = ci * OZ_KC;
-        if (sl == 0) {
-            unsigned char *bb = bs + (ci & 1) * BCH;
-            for (int e = tid; e < OZ_S * OZ_TN * (OZ_KC / 8); e += OZ_NT) {
-                const int t = e / (OZ_TN * (OZ_KC / 8)), r = e % (OZ_TN * (OZ_KC / 8));
-                const int n = r / (OZ_KC / 8), g = r % (OZ_KC / 8);
-                oz_cp16(bb + t * BSL + kmajor_off<KIND_BF16>(n, g * 8, OZ_KC),
-                        Bg + t * sb + (long long)(tn + n) * Z.Kp + kc + g * 8);
-            }
+    const int nc = Z.Kp / OZ_KC;
+    // cp.async of chunk c's slices into buffer c & 1: A slices first, then B
+    auto load_chunk = [&](int c) {
+        unsigned char *buf = smem + (c & 1) * BUF;
+        const int kc = c * OZ_KC;
+        constexpr int G = OZ_KC / 8;                 // 16-byte rows per slice row
+        for (int e = tid; e < OZ_S * OZ_TM * G; e += OZ_NT) {
+            const int sl = e / (OZ_TM * G), r = e % (OZ_TM * G), m = r / G, g = r % G;
+            oz_cp16(buf + sl * ASL + kmajor_off<KIND_BF16>(m, g * 8, OZ_KC),
+                    Ag + sl * sa + (long long)(tm + m) * Z.Kp + kc + g * 8);
         }
-        unsigned char *ab = as + (j & 1) * ASL;
-        for (int e = tid; e < OZ_TM * (OZ_KC / 8); e += OZ_NT) {
-            const int m = e / (OZ_KC / 8), g = e % (OZ_KC / 8);
-            oz_cp16(ab + kmajor_off<KIND_BF16>(m, g * 8, OZ_KC), Ag + sl * sa + (long long)(tm + m) * Z.Kp + kc + g * 8);
+        for (int e = tid; e < OZ_S * OZ_TN * G; e += OZ_NT) {
+            const int t = e / (OZ_TN * G), r = e % (OZ_TN * G), n = r / G, g = r % G;
+            oz_cp16(buf + OZ_S * ASL + t * BSL + kmajor_off<KIND_BF16>(n, g * 8, OZ_KC),
+                    Bg + t * sb + (long long)(tn + n) * Z.Kp + kc + g * 8);
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    // stage j's MMAs complete (the k-th completion of barrier j & 1 is stage j = (j & 1) + 2k)
+    // chunk c's MMAs complete (the k-th completion of barrier c & 1 is chunk c = (c & 1) + 2k)
     int waited = -1;
-    auto wait_stage = [&](int j) -> bool {
-        if (j <= waited) return true;
-        waited = j;
-        return oz_wait(mbar + (j & 1), (uint32_t)((j >> 1) & 1));
+    auto wait_chunk = [&](int c) -> bool {
+        if (c <= waited) return true;
+        waited = c;
+        return oz_wait(mbar + (c & 1), (uint32_t)((c >> 1) & 1));
     };
     long long X[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) X[c] = 0;
     const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + half * 32;
-    bool ok = true;
-    load_stage(0);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    for (int j = 0; j < NS; ++j) {
-        const int ci = j / OZ_S, sl = j % OZ_S;
-        bool mine = true;
-        if (j + 1 < NS) {
-            // stage j - 1 used the buffers stage j + 1 loads into
-            if (j >= 1) mine = wait_stage(j - 1);
-            if (mine) load_stage(j + 1);
+    auto fold = [&](int c) {
+#pragma unroll 1
+        for (int d = 0; d < 6; ++d) {
+            if (!oz_folds(d, c, nc)) continue;
+            float v[32];
+            ld_row32(trow + d * OZ_TN, v);
+            const long long w = 1LL << (7 * (5 - d));
+#pragma unroll
+            for (int j = 0; j < 32; ++j) X[j] += (long long)__float2int_rn(v[j]) * w;
         }
-        asm volatile("cp.async.commit_group;\ncp.async.wait_group 1;\n" ::: "memory");
+    };
+    bool ok = true, mine = true;
+    load_chunk(0);
+    for (int c = 0; c < nc; ++c) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         ok = __syncthreads_and(mine) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (!ok) break;
+        bool folded = false;
+        for (int d = 0; d < 6 && c >= 1; ++d) folded |= oz_folds(d, c - 1, nc);
+        if (folded) {   // chunk c - 1's accumulators are read before chunk c resets them
+            ok = __syncthreads_and(wait_chunk(c - 1)) != 0;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (!ok) break;
+            fold(c - 1);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        }
         if (tid == 0) {
-            const uint32_t a0 = oz_smem_addr(as + (j & 1) * ASL), b0 = oz_smem_addr(bs + (ci & 1) * BCH);
-            for (int t = 0; t < OZ_S - sl; ++t) {
-                const int d = sl + t;
-                const bool reset = sl == 0 && ci % oz_period(d) == 0;
+            // descriptors are linear in the address (its >> 4 in the low bits):
+            // every MMA's is a base plus a compile-time offset
+            const uint32_t a0 = oz_smem_addr(smem + (c & 1) * BUF), b0 = a0 + OZ_S * ASL;
+            const uint64_t da0 = smem_desc(a0, lbo, sbo), db0 = smem_desc(b0, lbo, sbo);
+            uint32_t keep = 0;   // bit d: chunk c continues D_d's period
 #pragma unroll
-                for (int ks = 0; ks < OZ_KC / 16; ++ks) {
-                    const uint32_t step = ks * 2 * 128;
-                    const uint64_t da = smem_desc(a0 + step, lbo, sbo);
-                    const uint64_t db = smem_desc(b0 + t * BSL + step, lbo, sbo);
-                    mma(tmem + d * OZ_TN, da, db, idesc, (reset && ks == 0) ? 0u : 1u, KIND_BF16);
+            for (int d = 0; d < OZ_S; ++d) keep |= (c % oz_period(d) != 0 ? 1u : 0u) << d;
+#pragma unroll
+            for (int sl = 0; sl < OZ_S; ++sl) {
+#pragma unroll
+                for (int t = 0; t < OZ_S - sl; ++t) {
+#pragma unroll
+                    for (int ks = 0; ks < OZ_KC / 16; ++ks) {
+                        const uint64_t da = da0 + (uint64_t)((sl * ASL + ks * 256) >> 4);
+                        const uint64_t db = db0 + (uint64_t)((t * BSL + ks * 256) >> 4);
+                        const uint32_t acc = (sl == 0 && ks == 0) ? (keep >> t) & 1u : 1u;
+                        mma(tmem + (sl + t) * OZ_TN, da, db, idesc, acc, KIND_BF16);
+                    }
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                oz_smem_addr(mbar + (j & 1))));
+                oz_smem_addr(mbar + (c & 1))));
         }
-        if (sl != OZ_S - 1) continue;
-        // end of chunk ci: fold the accumulators whose period ends here
-        bool fold = ci == nc - 1;
-        for (int d = 0; d < 6; ++d) fold |= (ci + 1) % oz_period(d) == 0;
-        if (!fold) continue;
-        ok = __syncthreads_and(wait_stage(j)) != 0;
+        // chunk c - 1 frees the buffer chunk c + 1 loads into
+        if (c >= 1) mine = wait_chunk(c - 1);
+        if (c + 1 < nc && mine) load_chunk(c + 1);
+    }
+    if (ok) {
+        ok = __syncthreads_and(mine && wait_chunk(nc - 1)) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (!ok) break;
-#pragma unroll 1
-        for (int d = 0; d < 6; ++d) {
-            if ((ci + 1) % oz_period(d) != 0 && ci != nc - 1) continue;
-            float v[32];
-            ld_row32(trow + d * OZ_TN, v);
-            const int sh = 7 * (5 - d);
-#pragma unroll
-            for (int c = 0; c < 32; ++c) X[c] += (long long)__float2int_rn(v[c]) * (1LL << sh);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        if (ok) fold(nc - 1);
     }
     if (!ok && tid == 0) atomicExch(Z.err, 1);
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
+    // this thread's 32 products (X and the FP32 tail D_6 + 2^-7 D_7),
+    // staged for row-wise writes (the slice buffers are free)
+    constexpr int SLD = OZ_TN + 1;
+    long long *stX = (long long *)smem;                              // [OZ_TM][SLD]
+    float *stT = (float *)(smem + (size_t)OZ_TM * SLD * sizeof(long long));   // [OZ_TM][SLD]
     if (ok) {
-        // this thread's 32 products, staged for row-wise writes (the B buffers are free)
-        double *stage = (double *)smem;   // [OZ_TM][OZ_TN + 1]
         float v6[32], v7[32];
         ld_row32(trow + 6 * OZ_TN, v6);
         ld_row32(trow + 7 * OZ_TN, v7);
         const int r = quad * 32 + lane;
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-            const double tail = (double)v6[c] + (double)v7[c] * 0x1p-7;
-            stage[r * (OZ_TN + 1) + half * 32 + c] = (double)X[c] * 0x1p-49 + tail * 0x1p-56;
+            stX[r * SLD + half * 32 + c] = X[c];
+            stT[r * SLD + half * 32 + c] = v6[c] + v7[c] * 0x1p-7f;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
     if (!ok) return;
-    // epilogue: a warp per row, lanes along its 64 columns
-    const double *stage = (const double *)smem;
-    const ChildRef A = child_ref(L, L.ca[s]), B = child_ref(L, L.cb[s]);
-    const int ldt = L.np + L.m;
-    for (int r = warp; r < OZ_TM; r += OZ_NT / 32) {
-        const int P = tm + r;
-        if (P >= L.np) break;
-        const int chi = L.par_child[P], idx = L.par_idx[P];
-        const ChildRef &Xc = chi == 0 ? A : B;
-        const int ea = Z.Ea[(long long)s * Z.Mp + P];
-        double *Th = L.Th + (long long)s * L.np * ldt + (long long)P * ldt;
+    // epilogue: warp w takes rows w, w + 8, ..; lanes the columns lane, lane + 32
+    const MergeLevelDev &L = J.L;
+    ChildRef A{}, B{};
+    if (J.form) {
+        A = child_ref(L, L.ca[s]);
+        B = child_ref(L, L.cb[s]);
+    }
+    constexpr int RW = OZ_TM / (OZ_NT / 32);   // rows per warp (16)
+    int pc[2], pi[2], fb[2];
+    bool cv[2];
 #pragma unroll
-        for (int u = 0; u < OZ_TN / 32; ++u) {
-            const int c = u * 32 + lane, col = tn + c;
-            if (col >= ldt) continue;
-            double g;
-            if (col < L.np) g = (L.par_child[col] == chi) ? Xc.T[(long long)idx * Xc.ld + L.par_idx[col]] : 0.0;
-            else g = Xc.h[(long long)idx * Xc.ldh + (col - L.np)];
-            const int sc = ea + Z.Fb[(long long)s * Z.Np + col];
-            Th[col] = sc >= OZ_NONFINITE ? __longlong_as_double(0x7FF8000000000000LL)
-                                         : g + ldexp(stage[r * (OZ_TN + 1) + c], sc);
+    for (int u = 0; u < 2; ++u) {
+        const int col = tn + u * 32 + lane;
+        cv[u] = col < J.N;
+        pc[u] = (J.form && col < L.np) ? L.par_child[col] : -1;   // -1: a load column of h
+        pi[u] = (J.form && col < L.np) ? L.par_idx[col] : col - L.np;
+        fb[u] = cv[u] ? Z.Fb[(long long)s * Z.Np + col] : 0;
+    }
+    int rchi = 0, ridx = 0, rea = 0;
+    if (lane < RW) {
+        const int P = tm + warp + (OZ_NT / 32) * lane;
+        if (P < J.M) {
+            if (J.form) {
+                rchi = L.par_child[P];
+                ridx = L.par_idx[P];
+            }
+            rea = Z.Ea[(long long)s * Z.Mp + P];
+        }
+    }
+    // the gathered part G (the merge) or C (an update) of every row first, then the stores
+    double gv[RW][2];
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+        const int P = tm + warp + (OZ_NT / 32) * i;
+        const int chi = __shfl_sync(0xffffffffu, rchi, i), idx = __shfl_sync(0xffffffffu, ridx, i);
+        const ChildRef &Xc = chi == 0 ? A : B;
+        const double *crow = J.c + (long long)s * J.sc + (long long)P * J.ldc + tn;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            double g = 0.0;
+            if (P < J.M && cv[u]) {
+                if (!J.form) g = crow[u * 32 + lane];
+                else if (pc[u] < 0) g = Xc.h[(long long)idx * Xc.ldh + pi[u]];
+                else if (pc[u] == chi) g = Xc.T[(long long)idx * Xc.ld + pi[u]];
+            }
+            gv[i][u] = g;
+        }
+    }
+    const double sign = J.form ? 1.0 : -1.0;
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+        const int r = warp + (OZ_NT / 32) * i, P = tm + r;
+        const int ea = __shfl_sync(0xffffffffu, rea, i);
+        if (P >= J.M) break;
+        double *out = J.c + (long long)s * J.sc + (long long)P * J.ldc + tn;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!cv[u]) continue;
+            const int c = u * 32 + lane, sc = ea + fb[u];
+            double v;
+            if (sc >= OZ_NONFINITE) v = __longlong_as_double(0x7FF8000000000000LL);
+            else v = fma(sign, oz_scaled_i64(stX[r * SLD + c], sc - 49) + oz_scaled_f32(stT[r * SLD + c], sc - 56), gv[i][u]);
+            out[c] = v;
         }
     }
 }
 
 }  // namespace
 
-size_t ozaki_scratch_bytes(int nm, int np, int n3, int m) {
-    const long long Kp = (n3 + OZ_KC - 1) / OZ_KC * OZ_KC;
-    const long long Mp = (np + OZ_TM - 1) / OZ_TM * OZ_TM, Np = (np + m + OZ_TN - 1) / OZ_TN * OZ_TN;
+size_t ozaki_scratch_bytes(int nm, int M, int K, int N) {
+    const long long Kp = (K + OZ_KALIGN - 1) / OZ_KALIGN * OZ_KALIGN;
+    const long long Mp = (M + OZ_TM - 1) / OZ_TM * OZ_TM, Np = (N + OZ_TN - 1) / OZ_TN * OZ_TN;
     return (size_t)nm * (OZ_S * (Mp + Np) * Kp * 2 + (Mp + Np) * 4) + 256;
 }
 
-// n3 <= 8192 keeps the int64 fixed-point sum of the D_d below 2^63
+// K <= 8192 keeps the int64 fixed-point sum of the D_d below 2^63
 bool ozaki_applies(int np, int n3) { return n3 >= 64 && n3 <= 8192 && np >= 2 * OZ_TM; }
 
-OzakiScratch ozaki_layout(void *base, int nm, int np, int n3, int m, int *err) {
+OzakiScratch ozaki_layout(void *base, int nm, int M, int K, int N, int *err) {
     OzakiScratch Z{};
-    Z.Kp = (n3 + OZ_KC - 1) / OZ_KC * OZ_KC;
-    Z.Mp = (np + OZ_TM - 1) / OZ_TM * OZ_TM;
-    Z.Np = (np + m + OZ_TN - 1) / OZ_TN * OZ_TN;
+    Z.Kp = (K + OZ_KALIGN - 1) / OZ_KALIGN * OZ_KALIGN;
+    Z.Mp = (M + OZ_TM - 1) / OZ_TM * OZ_TM;
+    Z.Np = (N + OZ_TN - 1) / OZ_TN * OZ_TN;
     unsigned char *b = (unsigned char *)base;
     Z.As = (__nv_bfloat16 *)b;
     b += (size_t)nm * OZ_S * Z.Mp * Z.Kp * 2;
@@ -404,17 +496,38 @@ OzakiScratch ozaki_layout(void *base, int nm, int np, int n3, int m, int *err) {
     return Z;
 }
 
-cudaError_t launch_parent_ozaki(const MergeLevelDev &L, const OzakiScratch &Z, cudaStream_t st) {
-    oz_slice_a<<<dim3((Z.Mp * 32 + 255) / 256, L.nm), 256, 0, st>>>(L, Z);
-    oz_colexp_b<<<dim3((Z.Np + 255) / 256, L.nm), 256, 0, st>>>(L, Z);
-    oz_slice_b<<<dim3(Z.Np / 32, Z.Kp / 64, L.nm), 256, 0, st>>>(L, Z);
+cudaError_t launch_ozaki(const OzJob &J, const OzakiScratch &Z0, cudaStream_t st) {
+    if (J.M <= 0 || J.N <= 0 || J.K <= 0) return cudaSuccess;
+    // the layout for this job's sizes, in the same scratch (sized for the largest job)
+    OzakiScratch Z = ozaki_layout(Z0.As, J.nm, J.M, J.K, J.N, Z0.err);
+    oz_slice_a<<<dim3((Z.Mp * 32 + 255) / 256, J.nm), 256, 0, st>>>(J, Z);
+    oz_colexp_b<<<dim3((Z.Np + 255) / 256, J.nm), 256, 0, st>>>(J, Z);
+    oz_slice_b<<<dim3(Z.Np / 32, Z.Kp / 64, J.nm), 256, 0, st>>>(J, Z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = 2 * (size_t)OZ_S * OZ_TN * OZ_KC * 2 + 2 * (size_t)OZ_TM * OZ_KC * 2 + 64;
+    const size_t smem = 2 * (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_KC * 2 + 64;
     e = cudaFuncSetAttribute(oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    oz_gemm<<<dim3(Z.Np / OZ_TN, Z.Mp / OZ_TM, L.nm), OZ_NT, smem, st>>>(L, Z);
+    oz_gemm<<<dim3(Z.Np / OZ_TN, Z.Mp / OZ_TM, J.nm), OZ_NT, smem, st>>>(J, Z);
     return cudaGetLastError();
+}
+
+cudaError_t launch_parent_ozaki(const MergeLevelDev &L, const OzakiScratch &Z, cudaStream_t st) {
+    OzJob J{};
+    J.nm = L.nm;
+    J.M = L.np;
+    J.K = L.n3;
+    J.N = L.np + L.m;
+    J.gather = 1;
+    J.b = L.aug + L.c3;
+    J.sb = (long long)L.n3 * L.lda;
+    J.ldb = L.lda;
+    J.form = 1;
+    J.c = L.Th;
+    J.ldc = L.np + L.m;
+    J.sc = (long long)L.np * J.ldc;
+    J.L = L;
+    return launch_ozaki(J, Z, st);
 }
 
 }  // namespace hps
