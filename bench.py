@@ -838,7 +838,7 @@ def run_gpu(args, rank, ws):
         reduced = {"merge_ms": t_merge / rs, "solve_ms": t_solve / rs, "merge_gflop": mflops / 1e9,
                    "merge_tflops": tf,
                    "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s", "frac": tf / 1.25,
-                                "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
+                                "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part; FP64 flops per second, the large products of which run FP64-accurate on the BF16 tensor cores (exact integer slices), so frac can exceed 1"},
                    "gpu_launches_merge": merge_launches, "flux_mismatch": flux_mismatch(w, lay, o, u, m),
                    "clocks": cs.summary()}
         # SlabLU (Section 2, Eq. (dell1)) on the same leaf maps and data
@@ -1048,7 +1048,7 @@ def slab_timing(w, plan, out, g, s, steps, warmup, ws):
     return {"slab_leaf_columns": s, "interfaces": w.nx // s - 1, "interface_nodes": w.ny * q,
             "factor_ms": t_f / steps, "solve_ms": t_s / steps, "factor_gflop": fl / 1e9, "factor_tflops": tf,
             "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s", "frac": tf / 1.25,
-                         "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
+                         "traffic": None, "peak_source": "nominal 1.25 TFLOP/s FP64 of the part; FP64 flops per second, the large products of which run FP64-accurate on the BF16 tensor cores (exact integer slices), so frac can exceed 1"},
             "gpu_launches_factor": launches, "flux_mismatch": flux_mismatch(w, plan.layout, out, u, m),
             "clocks": cs.summary()}, u
 
@@ -1137,7 +1137,7 @@ def run_merge_solve(args, rank, ws):
                           "merge_gflop": flops / 1e9,
                           "roofline": {"bound": "alu", "achieved": sp["merge_tflops"], "peak": pk, "unit": "TFLOP/s",
                                        "frac": sp["merge_tflops"] / pk, "traffic": None,
-                                       "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
+                                       "peak_source": "nominal 1.25 TFLOP/s FP64 of the part; FP64 flops per second, the large products of which run FP64-accurate on the BF16 tensor cores (exact integer slices), so frac can exceed 1"},
                           "levels": levels, "results": res}), flush=True)
 
 

@@ -15,11 +15,12 @@ from paper_2211_14969_b300 import workloads as WL
 pytestmark = pytest.mark.gpu
 
 
-def gpu_pipeline(w, prec="fp64", coef_fn=None, load_fn=None, g_fn=None, split=None):
+def gpu_pipeline(w, prec="fp64", coef_fn=None, load_fn=None, g_fn=None, split=None, tensor=True):
     p = int(w.p[0])
     plan = hps.Plan(w.p, w.boxes(), w.kappa)
     if split is not None:
         plan.set_merge_split(split)
+    plan.set_merge_tensor(tensor)
     coef, f, _ = gpu_inputs(w, plan, coef_fn, load_fn)
     out = plan.condense(coef, f, m=1, prec=prec, tol=1e-13, kmax=8)
     plan.merge(w.nx, w.ny, out["T"], out["h"], 1)
@@ -153,6 +154,27 @@ def test_larger_and_rectangular_grids_match_oracle(nx, ny, p):
     mask = np.ones(p * p, bool)
     mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
     assert rel(u_gpu[:, mask], u_ora[:, mask]) < 1e-11
+
+
+@pytest.mark.parametrize("p", [11])
+def test_tensor_core_merge_matches_oracle(p):
+    """32 x 32 leaves, p = 11, a root interface of 288 nodes (elimination
+    blocks of 128, 128 and 32 rows, the last one ragged): the root's split solve
+    with the right-hand side in blocks and tensor-core updates, and the
+    parents' maps of the levels below on the tensor cores, against the
+    oracle's merge tree; the FP64-pipe merge beside it."""
+    w = WL.bumps(p=p, nx=32, ny=32, kappa=30.0, seed=8, m=1)
+    w.dirichlet = "planewave"
+    sol, _, _ = oracle_pipeline(w)
+    u_ora = grid_from_sol(sol, p)
+    mask = np.ones(p * p, bool)
+    mask[[0, p - 1, (p - 1) * p, p * p - 1]] = False
+    errs = {}
+    for tensor in (True, False):
+        u_gpu = gpu_pipeline(w, tensor=tensor)
+        errs[tensor] = rel(u_gpu[:, mask], u_ora[:, mask])
+    print(f"p = {p}: tensor cores {errs[True]:.2e}, FP64 pipe {errs[False]:.2e}")
+    assert errs[True] < 1e-11 and errs[False] < 1e-11
 
 
 EVERY_LEVEL_SPLIT = 1 << 30
