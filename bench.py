@@ -1141,6 +1141,50 @@ def run_merge_solve(args, rank, ws):
                           "levels": levels, "results": res}), flush=True)
 
 
+def run_merge_kernels(args):
+    """Per-kernel device times of hps_merge (CUDA activity trace, no
+    replay), the parents' maps and right-hand-side updates on the tensor
+    cores and on the FP64 pipe; with --no-trace only the merges run."""
+    import torch
+    from paper_2211_14969_b300 import hps
+    from paper_2211_14969_b300 import workloads as WL
+    n = args.merge_kernels
+    w = WL.bumps_p20() if n == 64 else WL.bumps(p=20, nx=n, ny=n, kappa=200.0, seed=1, m=1)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f = make_inputs(w, plan)
+    out = plan.condense(coef, f, m=1, prec="fp64")
+    plan.set_merge_split(args.merge_split)
+    res = {}
+    for tensor in (True, False):
+        plan.set_merge_tensor(tensor)
+        for _ in range(max(1, args.warmup)):
+            plan.merge(w.nx, w.ny, out["T"], out["h"], 1)
+        torch.cuda.synchronize()
+        if args.no_trace:
+            continue
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            plan.merge(w.nx, w.ny, out["T"], out["h"], 1)
+            torch.cuda.synchronize()
+        agg = {}
+        for e in prof.events():
+            if e.device_type != torch.autograd.DeviceType.CUDA:
+                continue
+            k = e.name.replace("void ", "").replace("hps::", "").replace("(anonymous namespace)::", "").split("(")[0]
+            a = agg.setdefault(k, [0, 0.0])
+            a[0] += 1
+            a[1] += e.device_time_total / 1e3
+        total = sum(v[1] for v in agg.values())
+        res["tensor_cores" if tensor else "fp64_pipe"] = {
+            "kernel_ms_total": total,
+            "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total}
+                        for k, v in sorted(agg.items(), key=lambda kv: -kv[1][1])}}
+    plan.close()
+    if not args.no_trace:
+        print(json.dumps({"mode": "merge kernel breakdown", "grid": [w.nx, w.ny], "p": 20,
+                          "merge_split": args.merge_split, "results": res}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1164,9 +1208,17 @@ def main(argv=None):
                          "SlabLU (hps_slab_factor + hps_slab_solve) for slab widths 4, 8, 16")
     ap.add_argument("--leaf-solve", action="store_true",
                     help="time the leaf solve after the reduced solve: stored S vs re-factored leaves")
+    ap.add_argument("--merge-kernels", type=int, default=0, metavar="N",
+                    help="profiling mode: hps_merge on an N x N grid of p = 20 leaves (64: bumps_p20), one kernel "
+                         "breakdown per parent-map path from the CUDA activity trace")
+    ap.add_argument("--merge-split", type=int, default=-1,
+                    help="with --merge-kernels: hps_set_merge_split (0: one CTA per merge, a single stream)")
+    ap.add_argument("--no-trace", action="store_true", help="with --merge-kernels: run the merges only (for ncu)")
     args = ap.parse_args(argv)
     rank, ws = dist_setup()
-    if args.leaf_solve:
+    if args.merge_kernels:
+        run_merge_kernels(args)
+    elif args.leaf_solve:
         run_leaf_solve(args, rank, ws)
     elif args.merge_solve:
         run_merge_solve(args, rank, ws)
