@@ -252,17 +252,30 @@ hps_status hps_slab_factor(hps_plan *plan, int nx, int ny, int s, const double *
 hps_status hps_slab_solve(hps_plan *plan, const double *d_g, const double *d_S, const double *d_W, int m, double *d_u,
                           hps_stream stream);
 
-/* How hps_merge (and hps_merge_boxes, hps_slab_factor's slab merges) form
- * the parents' maps [T | h] = gather + [Ta13; Tb23] [S3 | w3] (the merge of
- * Section 2 above).  enable = 1 (default): levels whose shared edge has at
- * least 128 nodes and whose parent boundary at least 256 run this product
- * on the BF16 tensor cores, FP64-accurate: every row of [Ta13; Tb23] and
- * every column of [S3 | w3] is scaled by a power of two and cut into eight
- * 7-bit integer slices (exact in BF16); the 36 slice products with s + t
- * below 8 accumulate exactly in FP32 over K-chunks of 128 and are summed in
- * FP64 (error below 2^-53 relative to sum_k |a_ik| |b_kj|).  enable = 0:
- * every level on the FP64 pipe.  A tensor-core wait that times out makes
- * the merge return HPS_ERR_CUDA.  HPS_ERR_ARG for other values. */
+/* Where the large dense products of the merge (Section 2 above) run.
+ * enable = 1 (default): on the BF16 tensor cores, FP64-accurate, for
+ *   - the parents' maps [T | h] = gather + [Ta13; Tb23] [S3 | w3] of the
+ *     levels whose shared edge has 64 to 8192 nodes and whose parent
+ *     boundary at least 256 (hps_merge, hps_merge_boxes, the merges inside
+ *     hps_slab_factor's slabs), and
+ *   - the right-hand-side updates of the merge tree's solves over many CTAs
+ *     with shared edges of 256 to 8192 nodes: the right-hand side is
+ *     eliminated in blocks of 128 rows, each block's rows below (forward)
+ *     and above (backward) updated in one product.
+ *   Each row of the left factor and each column of the right one is scaled
+ *   by a power of two and cut into eight 7-bit integer slices (exact in
+ *   BF16); the 36 slice products of order s + t < 8 accumulate in FP32 in
+ *   tensor memory (exactly for s + t <= 5, folded into int64) and are added
+ *   to the FP64 data they update.  The error of one product is a few
+ *   2^-56 K max_k|a_ik| max_k|b_kj|: FP64's where a row / column is of even
+ *   magnitude, larger where it spans many orders of magnitude.
+ * enable = 2: as 1, and also SlabLU's interface solves (hps_slab_factor),
+ *   whose right-hand sides [-U_k | I] have such columns (measured: 4 x 128
+ *   leaves, p = 20, one interface of 2304 nodes, a flux mismatch of 6e-12
+ *   against 3e-13 on the FP64 pipe).
+ * enable = 0: every product on the FP64 pipe.
+ * A tensor-core wait that times out makes the call return HPS_ERR_CUDA.
+ * HPS_ERR_ARG for other values. */
 hps_status hps_set_merge_tensor(hps_plan *plan, int enable);
 
 /* How hps_merge solves Z [S3 | w3] = -[Ta31 Tb32 | ha3 + hb3] (the merge

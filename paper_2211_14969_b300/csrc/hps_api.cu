@@ -139,7 +139,7 @@ struct hps_plan {
     int slab_nx = 0, slab_ny = 0, slab_s = 0, slab_m = -1;
     bool slabbed = false;
     int split_below = -1;  // levels with fewer merges solve Z over many CTAs; -1: the SM count
-    int merge_tensor = 1;  // parents' [T | h] of large levels on the tensor cores (ozaki.cu)
+    int merge_tensor = 1;  // large merge products on the tensor cores (ozaki.cu); 2: SlabLU's interface solves too
     DevBuf oz_err;         // their timeout flag
     DevBuf slab_oz;        // tensor-core scratch of SlabLU's interface solves
     SplitAux split_aux{nullptr, nullptr, nullptr};   // look-ahead stream and events, made on first use
@@ -926,7 +926,7 @@ hps_status hps_merge_boxes(hps_plan *P, int nx, int ny, int wx0, int wy0, const 
 }
 
 hps_status hps_set_merge_tensor(hps_plan *P, int enable) {
-    if (P == nullptr || enable < 0 || enable > 1) return HPS_ERR_ARG;
+    if (P == nullptr || enable < 0 || enable > 2) return HPS_ERR_ARG;
     P->merge_tensor = enable;
     return HPS_OK;
 }
@@ -1034,7 +1034,7 @@ hps_status hps_slab_factor(hps_plan *P, int nx, int ny, int s, const double *d_T
         }
         double *aug = (double *)P->slab_aug.p;
         const double *th = (const double *)P->slab_th.p;
-        const bool blocked = split && P->merge_tensor && split_solve_blocked(n, 2 * n + m);
+        const bool blocked = split && P->merge_tensor == 2 && split_solve_blocked(n, 2 * n + m);
         OzakiScratch oz{};
         if (blocked) {
             if ((e = P->slab_oz.ensure(split_solve_scratch(1, n, 2 * n + m))) != cudaSuccess ||

@@ -181,6 +181,58 @@ __global__ void __launch_bounds__(CNT) split_swap_cols(double *__restrict__ aug,
     }
 }
 
+// The triangular solve of one elimination block for the right-hand side:
+// rows [b0, b0 + nb) of the columns [c0, C), nb <= kSplitKB, in place;
+// UPPER: X = U^{-1} Y with the block's upper triangle, else Y = L^{-1} Y
+// with its unit-lower triangle.  A CTA holds the triangle and a slab of
+// TW columns in shared memory; thread t updates column t % TW and the rows
+// congruent to t / TW modulo 256 / TW, one pivot row after the other.
+constexpr int TW = 32;
+template <bool UPPER>
+__global__ void __launch_bounds__(256, 1) split_block_trsm(double *__restrict__ aug, long long stride, int lda, int b0,
+                                                           int nb, int c0, int C) {
+    extern __shared__ double sm[];
+    const int ldt = nb | 1;
+    double *Tr = sm;                            // [nb][ldt]
+    double *Y = sm + (size_t)nb * ldt;          // [nb][TW]
+    const int s = blockIdx.y, cb = c0 + blockIdx.x * TW;
+    const double *A = aug + (long long)s * stride;
+    for (int e = threadIdx.x; e < nb * nb; e += 256) {
+        const int i = e / nb, j = e % nb;
+        Tr[i * ldt + j] = A[(long long)(b0 + i) * lda + b0 + j];
+    }
+    for (int e = threadIdx.x; e < nb * TW; e += 256) {
+        const int i = e / TW, c = e % TW;
+        Y[e] = cb + c < C ? A[(long long)(b0 + i) * lda + cb + c] : 0.0;
+    }
+    __syncthreads();
+    const int c = threadIdx.x % TW, r0 = threadIdx.x / TW;
+    constexpr int RS = 256 / TW;   // rows per thread step; row i belongs to the threads with r0 = i % RS
+    if (!UPPER) {
+        for (int j = 0; j < nb - 1; ++j) {
+            const double x = Y[j * TW + c];
+            for (int i = j + 1 + ((r0 - (j + 1)) % RS + RS) % RS; i < nb; i += RS)
+                Y[i * TW + c] = fma(-Tr[i * ldt + j], x, Y[i * TW + c]);
+            __syncthreads();
+        }
+    } else {
+        // one division per row and column, by the row's owner (the FP64 pipe
+        // is the bound here), then the updates of the rows above
+        for (int j = nb - 1; j >= 0; --j) {
+            if (r0 == j % RS) Y[j * TW + c] /= Tr[j * ldt + j];
+            __syncthreads();
+            const double x = Y[j * TW + c];
+            for (int i = r0; i < j; i += RS) Y[i * TW + c] = fma(-Tr[i * ldt + j], x, Y[i * TW + c]);
+        }
+        __syncthreads();
+    }
+    double *W = aug + (long long)s * stride;
+    for (int e = threadIdx.x; e < nb * TW; e += 256) {
+        const int i = e / TW, cc = e % TW;
+        if (cb + cc < C) W[(long long)(b0 + i) * lda + cb + cc] = Y[e];
+    }
+}
+
 // X1 = U11^{-1} Y1 for the right-hand columns of block row kb.
 template <int NB>
 __global__ void __launch_bounds__(CNT) split_upper(double *__restrict__ aug, long long stride, int lda, int kb, int nbk,
@@ -300,10 +352,13 @@ __global__ void __launch_bounds__(256) split_gemm_n16(double *__restrict__ aug, 
 
 }  // namespace
 
-constexpr int kSplitNB = 16;
-constexpr int kSplitKB = 128;   // elimination block of the right-hand side with oz_solve (a multiple of kSplitNB)
+constexpr int kSplitKB = 128;   // elimination block of the right-hand side with oz_solve (a multiple of the panel width)
 
-bool split_solve_fits(int n3) { return (size_t)((n3 | 1) * kSplitNB) * sizeof(double) <= 200 * 1024; }
+// panel width: 16 columns while a panel of the whole height fits the
+// panel kernel's shared memory, else 8 (interfaces of up to 3200 nodes)
+static bool panel_fits(int n3, int nb) { return (size_t)((n3 | 1) * nb) * sizeof(double) <= 200 * 1024; }
+static int split_nb(int n3) { return panel_fits(n3, 16) ? 16 : 8; }
+bool split_solve_fits(int n3) { return panel_fits(n3, 8); }
 
 bool split_solve_blocked(int n3, int nrhs) { return n3 >= 2 * kSplitKB && n3 <= 8192 && nrhs >= kSplitKB; }
 
@@ -311,7 +366,7 @@ size_t split_solve_scratch(int nm, int n3, int nrhs) { return ozaki_scratch_byte
 
 // the kernels launch_split_solve issues (an Ozaki job is four)
 int split_solve_launches(int n3, int nrhs, bool blocked, bool aux) {
-    constexpr int NB = kSplitNB;
+    const int NB = split_nb(n3);
     const int CZ = blocked ? n3 : n3 + nrhs;   // columns past the panel the LU steps touch, counted from 0
     int n = 0, kb0 = 0;
     for (int k = 0; k < n3; k += NB) {
@@ -321,31 +376,37 @@ int split_solve_launches(int n3, int nrhs, bool blocked, bool aux) {
         if (nr > 0 && cr > 0) n += (aux && cr > (nr < NB ? nr : NB)) ? 2 : 1;
         const int kb1 = k + nbk;
         if (blocked && (kb1 - kb0 == kSplitKB || kb1 == n3)) {
-            n += 1;
-            for (int j = kb0; j < kb1; j += NB) n += 1 + (j + NB < kb1);
+            n += 2;   // interchanges, block solve
             if (kb1 < n3) n += 4;
             kb0 = kb1;
         }
     }
     if (!blocked) return n + 2 * ((n3 + NB - 1) / NB) - 1;
     for (int b0 = ((n3 - 1) / kSplitKB) * kSplitKB; b0 >= 0; b0 -= kSplitKB) {
-        const int b1 = b0 + kSplitKB < n3 ? b0 + kSplitKB : n3;
-        for (int kb = ((b1 - 1) / NB) * NB; kb >= b0; kb -= NB) n += 1 + (kb > b0);
-        if (b0 > 0) n += 4;
+        n += 1 + (b0 > 0 ? 4 : 0);
     }
     return n;
 }
 
-cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t st, const SplitAux *aux) {
-    constexpr int NB = kSplitNB;
+template <int NB>
+static cudaError_t split_solve_nb(const MergeLevelDev &L, int *ipiv, cudaStream_t st, const SplitAux *aux) {
     const int n3 = L.n3, lda = L.lda, nm = L.nm;
     const int C = L.c3 + L.np + L.m;
     const long long stride = (long long)n3 * lda;
-    if (ipiv == nullptr || !split_solve_fits(n3)) return cudaErrorInvalidValue;
+    if (ipiv == nullptr || !panel_fits(n3, NB)) return cudaErrorInvalidValue;
     const size_t psmem = (size_t)((n3 | 1) * NB) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(split_panel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(L.info, 0, (size_t)nm * sizeof(int), st)) != cudaSuccess) return e;
+    auto trsm_smem = [](int nb) { return (size_t)nb * ((nb | 1) + TW) * sizeof(double); };
+    if (L.oz_solve) {
+        const int mx = (int)trsm_smem(kSplitKB);
+        if ((e = cudaFuncSetAttribute(split_block_trsm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(split_block_trsm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+                cudaSuccess)
+            return e;
+    }
     auto gemm = [&](cudaStream_t s, int r0, int nr, int c0, int nc, int ka, int kb, int K) {
         split_gemm<NB><<<dim3((nc + GT - 1) / GT, (nr + GT - 1) / GT, nm), 256, 0, s>>>(L.aug, stride, lda, r0, nr, c0,
                                                                                         nc, ka, kb, K);
@@ -415,12 +476,8 @@ cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s
             // order, the unit-lower solve inside the block, the rows below
             split_swap_cols<<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, kb0, kb1 - kb0,
                                                                               L.c3, C, ipiv);
-            for (int j = kb0; j < kb1; j += NB) {
-                const int w = kb1 - j < NB ? kb1 - j : NB;
-                split_swap_lower<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, n3, lda, j, w,
-                                                                                       L.c3, C, ipiv, 0);
-                if (j + w < kb1) gemm(st, j + w, kb1 - (j + w), L.c3, nrhs, j, j, w);
-            }
+            split_block_trsm<false><<<dim3((nrhs + TW - 1) / TW, nm), 256, trsm_smem(kb1 - kb0), st>>>(
+                L.aug, stride, lda, kb0, kb1 - kb0, L.c3, C);
             if (kb1 < n3 && (e = rhs_update(kb1, n3 - kb1, kb0, kb1 - kb0)) != cudaSuccess) return e;
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             kb0 = kb1;
@@ -441,15 +498,16 @@ cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t s
     // one tensor-core update of every row above it
     for (int b0 = ((n3 - 1) / kSplitKB) * kSplitKB; b0 >= 0; b0 -= kSplitKB) {
         const int b1 = b0 + kSplitKB < n3 ? b0 + kSplitKB : n3;
-        for (int kb = ((b1 - 1) / NB) * NB; kb >= b0; kb -= NB) {
-            const int nbk = b1 - kb < NB ? b1 - kb : NB;
-            split_upper<NB><<<dim3((nrhs + CNT - 1) / CNT, nm), CNT, 0, st>>>(L.aug, stride, lda, kb, nbk, L.c3, C);
-            if (kb > b0) gemm(st, b0, kb - b0, L.c3, nrhs, kb, kb, nbk);
-        }
+        split_block_trsm<true><<<dim3((nrhs + TW - 1) / TW, nm), 256, trsm_smem(b1 - b0), st>>>(L.aug, stride, lda, b0,
+                                                                                             b1 - b0, L.c3, C);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (b0 > 0 && (e = rhs_update(0, b0, b0, b1 - b0)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_split_solve(const MergeLevelDev &L, int *ipiv, cudaStream_t st, const SplitAux *aux) {
+    return split_nb(L.n3) == 16 ? split_solve_nb<16>(L, ipiv, st, aux) : split_solve_nb<8>(L, ipiv, st, aux);
 }
 
 }  // namespace hps

@@ -236,9 +236,10 @@ class Plan:
         self.check(load_library().hps_set_refine_stop(self.handle, int(bool(residual))), "hps_set_refine_stop")
 
     def set_merge_tensor(self, on=True):
-        """Parents' maps of the large merge levels on the tensor cores
-        (FP64-accurate integer slices, default) or on the FP64 pipe."""
-        self.check(load_library().hps_set_merge_tensor(self.handle, int(bool(on))), "hps_set_merge_tensor")
+        """The merge's large products on the tensor cores (FP64-accurate
+        integer slices; True or 1, the default), also SlabLU's interface
+        solves (2), or all on the FP64 pipe (False or 0)."""
+        self.check(load_library().hps_set_merge_tensor(self.handle, int(on)), "hps_set_merge_tensor")
 
     def set_merge_split(self, below=-1):
         """Levels with fewer than `below` merges solve over many CTAs (-1: SM count; 0: never)."""

@@ -105,3 +105,35 @@ def test_full_size_slab_against_tree():
     print(f"slab vs tree {diff:.2e}, flux mismatch {mismatch:.2e}")
     assert mismatch < 1e-12 and diff < 1e-9
     plan.close()
+
+
+def test_large_interface_narrow_panels():
+    """4 x 128 leaves, p = 20, slabs of 2 leaf columns: one interface of
+    2304 nodes, above what a 16-column panel of the split solve holds in
+    shared memory, so it factors with 8-column panels.  Against the merge
+    tree; the flux continuity of SlabLU's solution with the default tensor
+    path (the slab merges on the tensor cores, the interface solve on the
+    FP64 pipe) within a few times that of the all-FP64 factorization; with
+    the interface solve's right-hand side on the tensor cores as well
+    (mode 2) it is measurably larger here (the columns of [-U | I] span many
+    orders of magnitude) but still far inside the solve's bar."""
+    import bench
+    w = workload(4, 128, 20)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    out = plan.condense(coef, f, m=1)
+    g = torch.from_numpy(outer_g(w)[1]).cuda()
+    plan.merge(w.nx, w.ny, out["T"], out["h"], 1)
+    u_tree = plan.solve(g, out["S"], out["W"], 1).clone()
+    mism, diff = {}, {}
+    for mode in (0, 1, 2):
+        plan.set_merge_tensor(mode)
+        plan.slab_factor(w.nx, w.ny, 2, out["T"], out["h"], 1)
+        u = plan.slab_solve(g, out["S"], out["W"], 1)
+        torch.cuda.synchronize()
+        mism[mode] = bench.flux_mismatch(w, plan.layout, out, u, 1)
+        diff[mode] = float((u - u_tree).norm() / u_tree.norm())
+    print(f"slab vs tree {diff}, flux mismatch {mism}")
+    assert max(diff.values()) < 1e-10
+    assert mism[0] < 1e-10 and mism[1] < max(4 * mism[0], 1e-12) and mism[2] < 1e-10
+    plan.close()
