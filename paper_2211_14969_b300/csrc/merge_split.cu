@@ -27,6 +27,16 @@
 // The multipliers of L are not applied to earlier columns: the right-hand
 // side is eliminated together with Z, so L is never needed again and the
 // columns left of a panel keep its multipliers in their unswapped rows.
+//
+// With oz_solve (large interfaces, tensor path on) the steps above touch
+// only Z's columns; the right-hand side is eliminated per block of
+// kSplitKB rows instead: the block's interchanges in order (split_swap_cols,
+// which also applies each panel's interchanges to the block's earlier L
+// columns), its unit-lower solve in one kernel (split_block_trsm), and one
+// FP64-accurate tensor-core update of all rows below (ozaki.cu); the back
+// substitution likewise per block from the bottom, updating the rows above.
+// Panels are 16 columns wide, 8 where 16 do not fit the panel kernel's
+// shared memory (interfaces of 1601 to 3200 nodes).
 // info[s] receives the first step with an exactly zero pivot (1-based),
 // as LAPACK's getrf does; the elimination then continues without scaling.
 #include <cuda_runtime.h>
@@ -195,6 +205,7 @@ __global__ void __launch_bounds__(256, 1) split_block_trsm(double *__restrict__ 
     const int ldt = nb | 1;
     double *Tr = sm;                            // [nb][ldt]
     double *Y = sm + (size_t)nb * ldt;          // [nb][TW]
+    double *rd = Y + (size_t)nb * TW;           // [nb] reciprocals of U's diagonal
     const int s = blockIdx.y, cb = c0 + blockIdx.x * TW;
     const double *A = aug + (long long)s * stride;
     for (int e = threadIdx.x; e < nb * nb; e += 256) {
@@ -205,6 +216,8 @@ __global__ void __launch_bounds__(256, 1) split_block_trsm(double *__restrict__ 
         const int i = e / TW, c = e % TW;
         Y[e] = cb + c < C ? A[(long long)(b0 + i) * lda + cb + c] : 0.0;
     }
+    if (UPPER)
+        for (int j = threadIdx.x; j < nb; j += 256) rd[j] = 1.0 / A[(long long)(b0 + j) * lda + b0 + j];
     __syncthreads();
     const int c = threadIdx.x % TW, r0 = threadIdx.x / TW;
     constexpr int RS = 256 / TW;   // rows per thread step; row i belongs to the threads with r0 = i % RS
@@ -216,10 +229,11 @@ __global__ void __launch_bounds__(256, 1) split_block_trsm(double *__restrict__ 
             __syncthreads();
         }
     } else {
-        // one division per row and column, by the row's owner (the FP64 pipe
-        // is the bound here), then the updates of the rows above
+        // the row's owner scales it by the diagonal's reciprocal (one division
+        // per row and CTA: the FP64 pipe is the bound here), then the rows
+        // above are updated
         for (int j = nb - 1; j >= 0; --j) {
-            if (r0 == j % RS) Y[j * TW + c] /= Tr[j * ldt + j];
+            if (r0 == j % RS) Y[j * TW + c] *= rd[j];
             __syncthreads();
             const double x = Y[j * TW + c];
             for (int i = r0; i < j; i += RS) Y[i * TW + c] = fma(-Tr[i * ldt + j], x, Y[i * TW + c]);
@@ -398,7 +412,7 @@ static cudaError_t split_solve_nb(const MergeLevelDev &L, int *ipiv, cudaStream_
     cudaError_t e = cudaFuncSetAttribute(split_panel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(L.info, 0, (size_t)nm * sizeof(int), st)) != cudaSuccess) return e;
-    auto trsm_smem = [](int nb) { return (size_t)nb * ((nb | 1) + TW) * sizeof(double); };
+    auto trsm_smem = [](int nb) { return (size_t)nb * ((nb | 1) + TW + 1) * sizeof(double); };
     if (L.oz_solve) {
         const int mx = (int)trsm_smem(kSplitKB);
         if ((e = cudaFuncSetAttribute(split_block_trsm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
