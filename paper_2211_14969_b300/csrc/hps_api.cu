@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "hps.h"
@@ -803,11 +804,6 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
         return P->fail(HPS_ERR_ARG, std::string(who) + ": d_T required, d_h required when m > 0");
     const int q = P->pmin - 2;
     cudaStream_t s = (cudaStream_t)stream;
-    for (auto &L : P->levels) {
-        L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
-        L.piv.release(); L.u3.release(); L.oz.release();
-    }
-    P->levels.clear();
     P->merged = false;
     P->slabbed = false;
     const int split_below = P->split_below < 0 ? P->sms : P->split_below;
@@ -826,6 +822,13 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
         hl.push_back(H);
         if (dir == 0) wx *= 2; else wy *= 2;
     }
+    // the level buffers of an earlier call are kept (ensure() grows them);
+    // levels beyond this tree's depth are freed
+    for (size_t i = hl.size(); i < P->levels.size(); ++i) {
+        Level &L = P->levels[i];
+        L.maps.release(); L.aug.release(); L.th.release(); L.u.release(); L.info.release();
+        L.piv.release(); L.u3.release(); L.oz.release();
+    }
     P->levels.resize(hl.size());
     cudaError_t e = cudaSuccess;
     const int nbc0 = 2 * (wx0 + wy0) * q;   // boundary nodes of a unit box
@@ -842,17 +845,29 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
             e = cudaMemcpy2DAsync(d_root_Th + nbc0, (size_t)(nbc0 + m) * sizeof(double), d_h, (size_t)m * sizeof(double),
                                   (size_t)m * sizeof(double), nbc0, cudaMemcpyDeviceToDevice, s);
     }
-    for (size_t li = 0; li < hl.size(); ++li) {
+    // every level's index maps reach the device before the first launch, so
+    // the copies (from pageable memory, which wait for the stream) do not
+    // hold the host back between the levels' kernels
+    std::vector<std::vector<int>> all_maps(hl.size());
+    std::vector<std::array<size_t, 8>> offs(hl.size());
+    for (size_t li = 0; li < hl.size() && e == cudaSuccess; ++li) {
+        const HostLevel &H = hl[li];
+        std::vector<int> &maps = all_maps[li];
+        auto put = [&](const std::vector<int> &v) { size_t o = maps.size(); maps.insert(maps.end(), v.begin(), v.end()); return o; };
+        offs[li] = {put(H.ca), put(H.cb), put(H.par_child), put(H.par_idx), put(H.s3a), put(H.s3b), put(H.srca),
+                    put(H.srcb)};
+        if ((e = P->levels[li].maps.ensure(maps.size() * sizeof(int))) != cudaSuccess) break;
+        e = cudaMemcpyAsync(P->levels[li].maps.p, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (size_t li = 0; li < hl.size() && e == cudaSuccess; ++li) {
         const HostLevel &H = hl[li];
         Level &L = P->levels[li];
-        std::vector<int> maps;
-        auto put = [&](const std::vector<int> &v) { size_t o = maps.size(); maps.insert(maps.end(), v.begin(), v.end()); return o; };
-        const size_t oca = put(H.ca), ocb = put(H.cb), opc = put(H.par_child), opi = put(H.par_idx);
-        const size_t o3a = put(H.s3a), o3b = put(H.s3b), osa = put(H.srca), osb = put(H.srcb);
+        const size_t oca = offs[li][0], ocb = offs[li][1], opc = offs[li][2], opi = offs[li][3];
+        const size_t o3a = offs[li][4], o3b = offs[li][5], osa = offs[li][6], osb = offs[li][7];
         const bool root = li + 1 == hl.size();
         const bool form = !root || d_root_Th != nullptr;
         const int lda = (int)round_up(round_up(H.n3, 4) + H.np + m, 4);
-        if ((e = L.maps.ensure(maps.size() * sizeof(int))) != cudaSuccess) break;
         if ((e = L.aug.ensure((size_t)H.nm * H.n3 * lda * sizeof(double))) != cudaSuccess) break;
         if (!root && (e = L.th.ensure((size_t)H.nm * H.np * (H.np + m) * sizeof(double))) != cudaSuccess) break;
         if ((e = L.u.ensure((size_t)H.nm * H.np * std::max(m, 1) * sizeof(double))) != cudaSuccess) break;
@@ -860,8 +875,6 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
         if ((e = L.u3.ensure((size_t)H.nm * H.n3 * std::max(m, 1) * sizeof(double))) != cudaSuccess) break;
         const bool split = H.nm < split_below && split_solve_fits(H.n3);
         if (split && (e = L.piv.ensure((size_t)H.nm * H.n3 * sizeof(int))) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(L.maps.p, maps.data(), maps.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         const int *mp = (const int *)L.maps.p;
         MergeLevelDev &D = L.dev;
         D.nm = H.nm; D.n3 = H.n3; D.c3 = (int)round_up(H.n3, 4); D.np = H.np; D.nbc = H.nbc; D.m = m; D.lda = lda;

@@ -477,7 +477,7 @@ size_t ozaki_scratch_bytes(int nm, int M, int K, int N) {
 }
 
 // K <= 8192 keeps the int64 fixed-point sum of the D_d below 2^63
-bool ozaki_applies(int np, int n3) { return n3 >= 64 && n3 <= 8192 && np >= 2 * OZ_TM; }
+bool ozaki_applies(int np, int n3) { return n3 >= 16 && n3 <= 8192 && np >= 64; }
 
 OzakiScratch ozaki_layout(void *base, int nm, int M, int K, int N, int *err) {
     OzakiScratch Z{};
