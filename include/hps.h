@@ -255,8 +255,8 @@ hps_status hps_slab_solve(hps_plan *plan, const double *d_g, const double *d_S, 
 /* Where the large dense products of the merge (Section 2 above) run.
  * enable = 1 (default): on the BF16 tensor cores, FP64-accurate, for
  *   - the parents' maps [T | h] = gather + [Ta13; Tb23] [S3 | w3] of the
- *     levels whose shared edge has 64 to 8192 nodes and whose parent
- *     boundary at least 256 (hps_merge, hps_merge_boxes, the merges inside
+ *     levels whose shared edge has 16 to 8192 nodes and whose parent
+ *     boundary at least 64 (hps_merge, hps_merge_boxes, the merges inside
  *     hps_slab_factor's slabs), and
  *   - the right-hand-side updates of the merge tree's solves over many CTAs
  *     with shared edges of 256 to 8192 nodes: the right-hand side is
