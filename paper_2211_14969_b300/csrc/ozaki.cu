@@ -21,10 +21,10 @@
 // Kernels: the slices of A (a warp per row, the gather included) and of B
 // (column exponents, then slices transposed through shared memory so every
 // slice row is K-contiguous), integer bit operations only; then the GEMM:
-// one CTA of 256 threads per 128 x 64 output tile, K in chunks of 64, the
-// chunk's eight B slices (8 x 64 x 64) and one A slice (128 x 64) in shared
-// memory in the K-major no-swizzle core-matrix layout, both double-buffered
-// so the next stage's cp.async loads overlap the current stage's MMAs, eight
+// one CTA of 256 threads per 128 x 64 output tile, K in chunks of 16, each
+// chunk's eight A and eight B slices (48 KB) in shared memory in the K-major
+// no-swizzle core-matrix layout, four chunks in flight so a chunk's cp.async
+// loads overlap the MMAs of the three before it, eight
 // accumulators of 64 columns in TMEM (all 512 columns: one CTA per SM), one
 // thread issuing the MMAs, bounded mbarrier waits (a timeout skips the tile
 // and sets the error flag), and the epilogue staged through shared memory
@@ -41,7 +41,8 @@ namespace hps {
 namespace {
 
 constexpr int OZ_S = 8;       // slices per operand
-constexpr int OZ_KC = 32;     // K-chunk staged in shared memory
+constexpr int OZ_KC = 16;     // K-chunk staged in shared memory (one MMA K-step)
+constexpr int OZ_NBUF = 4;    // chunk buffers in flight
 constexpr int OZ_KALIGN = 64; // K padding: a multiple of OZ_KC and of the B-slicing tile
 constexpr int OZ_TM = 128, OZ_TN = 64;
 constexpr int OZ_NT = 256;
@@ -238,32 +239,32 @@ __device__ __forceinline__ double oz_scaled_f32(float t, int e) {
                                             ((unsigned long long)(b & 0x7FFFFFu) << 29)));
 }
 
-// Exactness periods of the FP32 accumulators, in K-chunks of OZ_KC = 32:
+// Exactness periods of the FP32 accumulators, in K-chunks of OZ_KC = 16:
 // D_d over K columns is a sum of at most (d + 1) K products of magnitude
 // <= 127^2, exact while (d + 1) K 127^2 < 2^24, i.e. K <= 1024, 512, 256,
 // 256, 128, 128 for d = 0..5.  D_6 and D_7 (weights 2^-56, 2^-63) stay in
 // tensor memory over the whole K: their FP32 rounding is below the FP64
 // product's own error bound.
 __device__ __forceinline__ int oz_period(int d) {
-    return d == 0 ? 32 : d == 1 ? 16 : d <= 3 ? 8 : d <= 5 ? 4 : 1 << 30;
+    return d == 0 ? 64 : d == 1 ? 32 : d <= 3 ? 16 : d <= 5 ? 8 : 1 << 30;
 }
 __device__ __forceinline__ bool oz_folds(int d, int c, int nc) { return (c + 1) % oz_period(d) == 0 || c == nc - 1; }
 
 // (A B)[P][c] = 2^(Ea_P + Fb_c) (2^-49 X + 2^-56 (D_6 + 2^-7 D_7)),
 // X = sum_{d <= 5} D_d 2^(7 (5 - d)) in exact int64 fixed point; the
 // epilogue writes the merge's Th = G + A B or updates C -= A B in place.
-// Chunk c: the 36 products of its eight A and eight B slices (72 MMAs of
-// K = 16), from buffer c & 1; chunk c + 1's loads are issued once chunk
-// c - 1's MMAs are done, and chunk c + 1's MMAs queue behind chunk c's,
-// except after a chunk whose accumulators are folded.
+// Chunk c: the 36 products of its eight A and eight B slices (36 MMAs of
+// K = 16), from buffer c % OZ_NBUF; chunk c + 3's loads are issued once
+// chunk c - 1's MMAs are done, and chunk c + 1's MMAs queue behind chunk
+// c's, except after a chunk whose accumulators are folded.
 __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
     extern __shared__ __align__(1024) unsigned char smem[];
     using namespace tc;
     constexpr int BSL = OZ_TN * OZ_KC * 2;           // one B slice tile, bytes
     constexpr int ASL = OZ_TM * OZ_KC * 2;           // one A slice tile
     constexpr int BUF = OZ_S * (ASL + BSL);          // one chunk: 8 A + 8 B slices
-    uint64_t *mbar = (uint64_t *)(smem + 2 * BUF);   // [2] MMA completion, one per buffer
-    uint32_t *tmem_p = (uint32_t *)(mbar + 2);
+    uint64_t *mbar = (uint64_t *)(smem + OZ_NBUF * BUF);   // [OZ_NBUF] MMA completion, one per buffer
+    uint32_t *tmem_p = (uint32_t *)(mbar + OZ_NBUF);
     const int s = blockIdx.z, tm = blockIdx.y * OZ_TM, tn = blockIdx.x * OZ_TN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;     // TMEM lanes 32 quad.., columns 32 half..
@@ -272,8 +273,8 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(oz_smem_addr(mbar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(oz_smem_addr(mbar + 1)));
+        for (int b = 0; b < OZ_NBUF; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(oz_smem_addr(mbar + b)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -286,9 +287,9 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
     const __nv_bfloat16 *Ag = Z.As + (long long)s * OZ_S * sa;
     const __nv_bfloat16 *Bg = Z.Bs + (long long)s * OZ_S * sb;
     const int nc = Z.Kp / OZ_KC;
-    // cp.async of chunk c's slices into buffer c & 1: A slices first, then B
+    // cp.async of chunk c's slices into buffer c % OZ_NBUF: A slices first, then B
     auto load_chunk = [&](int c) {
-        unsigned char *buf = smem + (c & 1) * BUF;
+        unsigned char *buf = smem + (c % OZ_NBUF) * BUF;
         const int kc = c * OZ_KC;
         constexpr int G = OZ_KC / 8;                 // 16-byte rows per slice row
         for (int e = tid; e < OZ_S * OZ_TM * G; e += OZ_NT) {
@@ -303,12 +304,12 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    // chunk c's MMAs complete (the k-th completion of barrier c & 1 is chunk c = (c & 1) + 2k)
+    // chunk c's MMAs complete (the k-th completion of barrier b is chunk c = b + OZ_NBUF k)
     int waited = -1;
     auto wait_chunk = [&](int c) -> bool {
         if (c <= waited) return true;
         waited = c;
-        return oz_wait(mbar + (c & 1), (uint32_t)((c >> 1) & 1));
+        return oz_wait(mbar + c % OZ_NBUF, (uint32_t)((c / OZ_NBUF) & 1));
     };
     long long X[32];
 #pragma unroll
@@ -326,9 +327,13 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
         }
     };
     bool ok = true, mine = true;
-    load_chunk(0);
+    for (int c = 0; c < OZ_NBUF - 1 && c < nc; ++c) load_chunk(c);
     for (int c = 0; c < nc; ++c) {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        // chunk c's group complete; the groups of chunks c + 1, c + 2 may be in flight
+        const int newer = nc - 1 - c < OZ_NBUF - 2 ? nc - 1 - c : OZ_NBUF - 2;
+        if (newer >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+        else if (newer == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         ok = __syncthreads_and(mine) != 0;
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
         if (tid == 0) {
             // descriptors are linear in the address (its >> 4 in the low bits):
             // every MMA's is a base plus a compile-time offset
-            const uint32_t a0 = oz_smem_addr(smem + (c & 1) * BUF), b0 = a0 + OZ_S * ASL;
+            const uint32_t a0 = oz_smem_addr(smem + (c % OZ_NBUF) * BUF), b0 = a0 + OZ_S * ASL;
             const uint64_t da0 = smem_desc(a0, lbo, sbo), db0 = smem_desc(b0, lbo, sbo);
             uint32_t keep = 0;   // bit d: chunk c continues D_d's period
 #pragma unroll
@@ -367,11 +372,11 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                oz_smem_addr(mbar + (c & 1))));
+                oz_smem_addr(mbar + c % OZ_NBUF)));
         }
-        // chunk c - 1 frees the buffer chunk c + 1 loads into
+        // chunk c - 1 frees the buffer chunk c + OZ_NBUF - 1 loads into
         if (c >= 1) mine = wait_chunk(c - 1);
-        if (c + 1 < nc && mine) load_chunk(c + 1);
+        if (c + OZ_NBUF - 1 < nc && mine) load_chunk(c + OZ_NBUF - 1);
     }
     if (ok) {
         ok = __syncthreads_and(mine && wait_chunk(nc - 1)) != 0;
@@ -505,7 +510,7 @@ cudaError_t launch_ozaki(const OzJob &J, const OzakiScratch &Z0, cudaStream_t st
     oz_slice_b<<<dim3(Z.Np / 32, Z.Kp / 64, J.nm), 256, 0, st>>>(J, Z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = 2 * (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_KC * 2 + 64;
+    const size_t smem = OZ_NBUF * (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_KC * 2 + 64;
     e = cudaFuncSetAttribute(oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     oz_gemm<<<dim3(Z.Np / OZ_TN, Z.Mp / OZ_TM, J.nm), OZ_NT, smem, st>>>(J, Z);
