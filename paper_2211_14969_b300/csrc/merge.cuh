@@ -16,6 +16,7 @@ struct OzakiScratch {
     int *Ea, *Fb;             // [nm][Mp], [nm][Np]
     int Kp, Mp, Np;
     int *err;                 // set when a tensor-core wait timed out
+    int tma;                  // the GEMM's loads by TMA boxes (tensor maps encoded), else cp.async
 };
 
 struct MergeLevelDev {

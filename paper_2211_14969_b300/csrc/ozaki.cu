@@ -29,9 +29,12 @@
 // thread issuing the MMAs, bounded mbarrier waits (a timeout skips the tile
 // and sets the error flag), and the epilogue staged through shared memory
 // for row-contiguous writes.
+#include <cuda.h>   // CUtensorMap and cuTensorMapEncodeTiled's types (called through the runtime's entry point)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "hps_internal.cuh"
 #include "merge.cuh"
@@ -44,6 +47,14 @@ constexpr int OZ_S = 8;       // slices per operand
 constexpr int OZ_KC = 16;     // K-chunk staged in shared memory (one MMA K-step)
 constexpr int OZ_NBUF = 4;    // chunk buffers in flight
 constexpr int OZ_KALIGN = 64; // K padding: a multiple of OZ_KC and of the B-slicing tile
+
+// Slice planes are stored in 8 x 8 tiles (8 rows, 8 consecutive k: 128
+// contiguous bytes), a row of tiles after the other: exactly the K-major
+// no-swizzle core-matrix layout of the MMA operands, so one chunk of a
+// 128-row block is 16 runs of 256 contiguous bytes (one TMA box).
+__host__ __device__ __forceinline__ long long oz_tile_off(int P, int k, int Kp) {
+    return ((long long)(P >> 3) * (Kp / 8) + (k >> 3)) * 64 + (P & 7) * 8 + (k & 7);
+}
 constexpr int OZ_TM = 128, OZ_TN = 64;
 constexpr int OZ_NT = 256;
 
@@ -125,7 +136,7 @@ __global__ void __launch_bounds__(256) oz_slice_a(OzJob J, OzakiScratch Z) {
     const int P = (blockIdx.x * 256 + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (P >= Z.Mp) return;
     const long long stride = (long long)Z.Mp * Z.Kp;
-    __nv_bfloat16 *row = Z.As + (long long)s * OZ_S * stride + (long long)P * Z.Kp;
+    __nv_bfloat16 *plane = Z.As + (long long)s * OZ_S * stride;
     const double *tr = nullptr;
     const int *s3 = nullptr;   // gathered rows: the row's entries at s3[k]
     int e = 0;
@@ -153,7 +164,7 @@ __global__ void __launch_bounds__(256) oz_slice_a(OzJob J, OzakiScratch Z) {
             const int k = g * 8 + i;
             x[i] = (tr && k < J.K) ? tr[s3 ? s3[k] : k] : 0.0;
         }
-        oz_store8(x, e, row + g * 8, stride);
+        oz_store8(x, e, plane + oz_tile_off(P, g * 8, Z.Kp), stride);
     }
     if (lane == 0) Z.Ea[(long long)s * Z.Mp + P] = e;
 }
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(256) oz_slice_b(OzJob J, OzakiScratch Z) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) x[i] = tile[g * 8 + i][cc];
     const long long stride = (long long)Z.Np * Z.Kp;
-    oz_store8(x, Z.Fb[(long long)s * Z.Np + c], Z.Bs + (long long)s * OZ_S * stride + (long long)c * Z.Kp + k0 + g * 8,
+    oz_store8(x, Z.Fb[(long long)s * Z.Np + c], Z.Bs + (long long)s * OZ_S * stride + oz_tile_off(c, k0 + g * 8, Z.Kp),
               stride);
 }
 
@@ -196,7 +207,21 @@ __device__ __forceinline__ void oz_cp16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(oz_smem_addr(dst)), "l"(src) : "memory");
 }
 
-// bounded wait on the MMA-completion mbarrier
+__device__ __forceinline__ void oz_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(oz_smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// one TMA box of a 3-D tensor map into shared memory, arrival on mbar
+__device__ __forceinline__ void oz_tma3(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(oz_smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(oz_smem_addr(mbar))
+        : "memory");
+}
+
+// bounded wait on an mbarrier phase
 __device__ __forceinline__ bool oz_wait(uint64_t *mbar, uint32_t phase) {
     uint32_t done = 0;
     for (int it = 0; it < (1 << 24) && !done; ++it) {
@@ -257,14 +282,16 @@ __device__ __forceinline__ bool oz_folds(int d, int c, int nc) { return (c + 1) 
 // K = 16), from buffer c % OZ_NBUF; chunk c + 3's loads are issued once
 // chunk c - 1's MMAs are done, and chunk c + 1's MMAs queue behind chunk
 // c's, except after a chunk whose accumulators are folded.
-__global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
+__global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z, const __grid_constant__ CUtensorMap tmA,
+                                                    const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ __align__(1024) unsigned char smem[];
     using namespace tc;
     constexpr int BSL = OZ_TN * OZ_KC * 2;           // one B slice tile, bytes
     constexpr int ASL = OZ_TM * OZ_KC * 2;           // one A slice tile
     constexpr int BUF = OZ_S * (ASL + BSL);          // one chunk: 8 A + 8 B slices
     uint64_t *mbar = (uint64_t *)(smem + OZ_NBUF * BUF);   // [OZ_NBUF] MMA completion, one per buffer
-    uint32_t *tmem_p = (uint32_t *)(mbar + OZ_NBUF);
+    uint64_t *full = mbar + OZ_NBUF;                       // [OZ_NBUF] TMA arrival, one per buffer
+    uint32_t *tmem_p = (uint32_t *)(full + OZ_NBUF);
     const int s = blockIdx.z, tm = blockIdx.y * OZ_TM, tn = blockIdx.x * OZ_TN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;     // TMEM lanes 32 quad.., columns 32 half..
@@ -273,8 +300,10 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        for (int b = 0; b < OZ_NBUF; ++b)
+        for (int b = 0; b < OZ_NBUF; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(oz_smem_addr(mbar + b)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(oz_smem_addr(full + b)));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -287,20 +316,31 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
     const __nv_bfloat16 *Ag = Z.As + (long long)s * OZ_S * sa;
     const __nv_bfloat16 *Bg = Z.Bs + (long long)s * OZ_S * sb;
     const int nc = Z.Kp / OZ_KC;
-    // cp.async of chunk c's slices into buffer c % OZ_NBUF: A slices first, then B
+    // chunk c's slices into buffer c % OZ_NBUF (A slices first, then B): one
+    // TMA box each, issued by thread 0 (arrival on full[]), or without a
+    // tensor map cp.async of the same 256-byte runs by every thread
+    int issued = 0;   // chunks whose loads were issued
     auto load_chunk = [&](int c) {
         unsigned char *buf = smem + (c % OZ_NBUF) * BUF;
         const int kc = c * OZ_KC;
-        constexpr int G = OZ_KC / 8;                 // 16-byte rows per slice row
-        for (int e = tid; e < OZ_S * OZ_TM * G; e += OZ_NT) {
-            const int sl = e / (OZ_TM * G), r = e % (OZ_TM * G), m = r / G, g = r % G;
-            oz_cp16(buf + sl * ASL + kmajor_off<KIND_BF16>(m, g * 8, OZ_KC),
-                    Ag + sl * sa + (long long)(tm + m) * Z.Kp + kc + g * 8);
+        issued = c + 1;
+        if (Z.tma) {
+            if (tid == 0) {
+                oz_expect_tx(full + c % OZ_NBUF, BUF);
+                oz_tma3(buf, &tmA, kc * 8, tm / 8, s * OZ_S, full + c % OZ_NBUF);
+                oz_tma3(buf + OZ_S * ASL, &tmB, kc * 8, tn / 8, s * OZ_S, full + c % OZ_NBUF);
+            }
+            return;
         }
-        for (int e = tid; e < OZ_S * OZ_TN * G; e += OZ_NT) {
-            const int t = e / (OZ_TN * G), r = e % (OZ_TN * G), n = r / G, g = r % G;
-            oz_cp16(buf + OZ_S * ASL + t * BSL + kmajor_off<KIND_BF16>(n, g * 8, OZ_KC),
-                    Bg + t * sb + (long long)(tn + n) * Z.Kp + kc + g * 8);
+        constexpr int RUN = OZ_KC;                   // 16-byte pieces per 256-byte run (one 8-row block)
+        for (int e = tid; e < OZ_S * (OZ_TM / 8) * RUN; e += OZ_NT) {
+            const int sl = e / ((OZ_TM / 8) * RUN), r = e % ((OZ_TM / 8) * RUN), ph = r / RUN, j = r % RUN;
+            oz_cp16(buf + sl * ASL + ph * RUN * 16 + j * 16, Ag + sl * sa + oz_tile_off(tm + ph * 8, kc, Z.Kp) + j * 8);
+        }
+        for (int e = tid; e < OZ_S * (OZ_TN / 8) * RUN; e += OZ_NT) {
+            const int t = e / ((OZ_TN / 8) * RUN), r = e % ((OZ_TN / 8) * RUN), ph = r / RUN, j = r % RUN;
+            oz_cp16(buf + OZ_S * ASL + t * BSL + ph * RUN * 16 + j * 16,
+                    Bg + t * sb + oz_tile_off(tn + ph * 8, kc, Z.Kp) + j * 8);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -327,13 +367,18 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
         }
     };
     bool ok = true, mine = true;
+    int consumed = 0;   // chunks whose arrival thread 0 waited for (TMA)
     for (int c = 0; c < OZ_NBUF - 1 && c < nc; ++c) load_chunk(c);
     for (int c = 0; c < nc; ++c) {
-        // chunk c's group complete; the groups of chunks c + 1, c + 2 may be in flight
-        const int newer = nc - 1 - c < OZ_NBUF - 2 ? nc - 1 - c : OZ_NBUF - 2;
-        if (newer >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
-        else if (newer == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        if (Z.tma) {   // thread 0 issues the MMAs: it alone waits for the chunk's arrival
+            if (tid == 0) mine = mine && oz_wait(full + c % OZ_NBUF, (uint32_t)((c / OZ_NBUF) & 1));
+            if (tid == 0) consumed = c + 1;
+        } else {       // chunk c's group complete; the groups of chunks c + 1, c + 2 may be in flight
+            const int newer = nc - 1 - c < OZ_NBUF - 2 ? nc - 1 - c : OZ_NBUF - 2;
+            if (newer >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+            else if (newer == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         ok = __syncthreads_and(mine) != 0;
@@ -384,6 +429,8 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z) {
         if (ok) fold(nc - 1);
     }
     if (!ok && tid == 0) atomicExch(Z.err, 1);
+    if (!ok && Z.tma && tid == 0)   // boxes still in flight land before the CTA ends (bounded)
+        for (int c = consumed; c < issued; ++c) oz_wait(full + c % OZ_NBUF, (uint32_t)((c / OZ_NBUF) & 1));
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     // this thread's 32 products (X and the FP32 tail D_6 + 2^-7 D_7),
@@ -501,6 +548,25 @@ OzakiScratch ozaki_layout(void *base, int nm, int M, int K, int N, int *err) {
     return Z;
 }
 
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, through the runtime (null if unavailable:
+// the GEMM then loads with cp.async)
+static EncodeTiled encode_tiled() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+    });
+    return fn;
+}
+
 cudaError_t launch_ozaki(const OzJob &J, const OzakiScratch &Z0, cudaStream_t st) {
     if (J.M <= 0 || J.N <= 0 || J.K <= 0) return cudaSuccess;
     // the layout for this job's sizes, in the same scratch (sized for the largest job)
@@ -510,10 +576,27 @@ cudaError_t launch_ozaki(const OzJob &J, const OzakiScratch &Z0, cudaStream_t st
     oz_slice_b<<<dim3(Z.Np / 32, Z.Kp / 64, J.nm), 256, 0, st>>>(J, Z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = OZ_NBUF * (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_KC * 2 + 64;
+    const size_t smem = OZ_NBUF * (size_t)OZ_S * (OZ_TM + OZ_TN) * OZ_KC * 2 + 128;
     e = cudaFuncSetAttribute(oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    oz_gemm<<<dim3(Z.Np / OZ_TN, Z.Mp / OZ_TM, J.nm), OZ_NT, smem, st>>>(J, Z);
+    // tensor maps of the two slice arrays: (k within a row of tiles, row block, slice plane)
+    CUtensorMap tmA{}, tmB{};
+    Z.tma = 0;
+    if (EncodeTiled fn = encode_tiled()) {
+        const cuuint32_t boxA[3] = {OZ_KC * 8, OZ_TM / 8, OZ_S}, boxB[3] = {OZ_KC * 8, OZ_TN / 8, OZ_S}, es[3] = {1, 1, 1};
+        const cuuint64_t dA[3] = {(cuuint64_t)Z.Kp * 8, (cuuint64_t)Z.Mp / 8, (cuuint64_t)J.nm * OZ_S};
+        const cuuint64_t dB[3] = {(cuuint64_t)Z.Kp * 8, (cuuint64_t)Z.Np / 8, (cuuint64_t)J.nm * OZ_S};
+        const cuuint64_t sA[2] = {(cuuint64_t)Z.Kp * 16, (cuuint64_t)Z.Mp * Z.Kp * 2};
+        const cuuint64_t sB[2] = {(cuuint64_t)Z.Kp * 16, (cuuint64_t)Z.Np * Z.Kp * 2};
+        const bool okA = fn(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Z.As, dA, sA, boxA, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        const bool okB = okA && fn(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Z.Bs, dB, sB, boxB, es,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        Z.tma = okA && okB;
+    }
+    oz_gemm<<<dim3(Z.Np / OZ_TN, Z.Mp / OZ_TM, J.nm), OZ_NT, smem, st>>>(J, Z, tmA, tmB);
     return cudaGetLastError();
 }
 
