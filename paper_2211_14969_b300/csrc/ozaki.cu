@@ -20,15 +20,17 @@
 //
 // Kernels: the slices of A (a warp per row, the gather included) and of B
 // (column exponents, then slices transposed through shared memory so every
-// slice row is K-contiguous), integer bit operations only; then the GEMM:
-// one CTA of 256 threads per 128 x 64 output tile, K in chunks of 16, each
-// chunk's eight A and eight B slices (48 KB) in shared memory in the K-major
-// no-swizzle core-matrix layout, four chunks in flight so a chunk's cp.async
-// loads overlap the MMAs of the three before it, eight
-// accumulators of 64 columns in TMEM (all 512 columns: one CTA per SM), one
-// thread issuing the MMAs, bounded mbarrier waits (a timeout skips the tile
-// and sets the error flag), and the epilogue staged through shared memory
-// for row-contiguous writes.
+// slice row is K-contiguous), integer bit operations only, each slice plane
+// stored in 8 x 8 core-matrix tiles; then the GEMM: one CTA of 256 threads
+// per 128 x 64 output tile, K in chunks of 16, each chunk's eight A and
+// eight B slices (48 KB) loaded as two TMA boxes (cp.async.bulk.tensor,
+// arrival on an mbarrier) straight into the K-major no-swizzle layout of the
+// MMA operands, four buffers (two chunks' MMAs queued while the next two
+// load), eight accumulators of 64 columns in TMEM (all 512 columns: one CTA
+// per SM), one thread issuing the MMAs, bounded mbarrier waits (a timeout
+// skips the tile and sets the error flag), and the epilogue staged through
+// shared memory for row-contiguous writes.  Without the driver's tensor-map
+// encoder the same loads run as cp.async.
 #include <cuda.h>   // CUtensorMap and cuTensorMapEncodeTiled's types (called through the runtime's entry point)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -207,6 +209,14 @@ __device__ __forceinline__ void oz_cp16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(oz_smem_addr(dst)), "l"(src) : "memory");
 }
 
+// one lane of a converged warp (the MMA and TMA issues run from warp 0 as a
+// whole, so their descriptors stay warp-uniform)
+__device__ __forceinline__ bool oz_elect() {
+    uint32_t p = 0;
+    asm volatile("{\n.reg .pred q;\nelect.sync _|q, 0xffffffff;\nselp.u32 %0, 1, 0, q;\n}\n" : "=r"(p));
+    return p != 0;
+}
+
 __device__ __forceinline__ void oz_expect_tx(uint64_t *mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(oz_smem_addr(mbar)), "r"(bytes)
                  : "memory");
@@ -279,9 +289,9 @@ __device__ __forceinline__ bool oz_folds(int d, int c, int nc) { return (c + 1) 
 // X = sum_{d <= 5} D_d 2^(7 (5 - d)) in exact int64 fixed point; the
 // epilogue writes the merge's Th = G + A B or updates C -= A B in place.
 // Chunk c: the 36 products of its eight A and eight B slices (36 MMAs of
-// K = 16), from buffer c % OZ_NBUF; chunk c + 3's loads are issued once
-// chunk c - 1's MMAs are done, and chunk c + 1's MMAs queue behind chunk
-// c's, except after a chunk whose accumulators are folded.
+// K = 16), from buffer c % OZ_NBUF; chunk c + 2's loads are issued once
+// chunk c - 2's MMAs are done, so two chunks' MMAs stay queued, except
+// after a chunk whose accumulators are folded.
 __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z, const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -325,7 +335,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z, con
         const int kc = c * OZ_KC;
         issued = c + 1;
         if (Z.tma) {
-            if (tid == 0) {
+            if (warp == 0 && oz_elect()) {
                 oz_expect_tx(full + c % OZ_NBUF, BUF);
                 oz_tma3(buf, &tmA, kc * 8, tm / 8, s * OZ_S, full + c % OZ_NBUF);
                 oz_tma3(buf + OZ_S * ASL, &tmB, kc * 8, tn / 8, s * OZ_S, full + c % OZ_NBUF);
@@ -368,24 +378,27 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z, con
     };
     bool ok = true, mine = true;
     int consumed = 0;   // chunks whose arrival thread 0 waited for (TMA)
-    for (int c = 0; c < OZ_NBUF - 1 && c < nc; ++c) load_chunk(c);
+    for (int c = 0; c < OZ_NBUF - 2 && c < nc; ++c) load_chunk(c);
     for (int c = 0; c < nc; ++c) {
         if (Z.tma) {   // thread 0 issues the MMAs: it alone waits for the chunk's arrival
-            if (tid == 0) mine = mine && oz_wait(full + c % OZ_NBUF, (uint32_t)((c / OZ_NBUF) & 1));
-            if (tid == 0) consumed = c + 1;
-        } else {       // chunk c's group complete; the groups of chunks c + 1, c + 2 may be in flight
-            const int newer = nc - 1 - c < OZ_NBUF - 2 ? nc - 1 - c : OZ_NBUF - 2;
-            if (newer >= 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
-            else if (newer == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            if (warp == 0) mine = mine && oz_wait(full + c % OZ_NBUF, (uint32_t)((c / OZ_NBUF) & 1));
+            if (warp == 0) consumed = c + 1;
+        } else {       // chunk c's group complete; chunk c + 1's may be in flight
+            if (c + 1 < nc) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
             else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        ok = __syncthreads_and(mine) != 0;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (!ok) break;
         bool folded = false;
         for (int d = 0; d < 6 && c >= 1; ++d) folded |= oz_folds(d, c - 1, nc);
+        // with TMA only thread 0 touches a chunk before its MMAs, so the CTA
+        // meets only where it folds; with cp.async every thread's copies of
+        // the chunk must be visible first
+        if (!Z.tma || folded) {
+            if (!Z.tma) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            ok = __syncthreads_and(mine) != 0;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (!ok) break;
+        }
         if (folded) {   // chunk c - 1's accumulators are read before chunk c resets them
             ok = __syncthreads_and(wait_chunk(c - 1)) != 0;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -395,14 +408,16 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z, con
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         }
-        if (tid == 0) {
+        if (warp == 0 && __all_sync(0xffffffffu, mine)) {
             // descriptors are linear in the address (its >> 4 in the low bits):
-            // every MMA's is a base plus a compile-time offset
+            // every MMA's is a base plus a compile-time offset; warp 0 holds
+            // them uniformly and one elected lane issues
             const uint32_t a0 = oz_smem_addr(smem + (c % OZ_NBUF) * BUF), b0 = a0 + OZ_S * ASL;
             const uint64_t da0 = smem_desc(a0, lbo, sbo), db0 = smem_desc(b0, lbo, sbo);
             uint32_t keep = 0;   // bit d: chunk c continues D_d's period
 #pragma unroll
             for (int d = 0; d < OZ_S; ++d) keep |= (c % oz_period(d) != 0 ? 1u : 0u) << d;
+            if (oz_elect()) {
 #pragma unroll
             for (int sl = 0; sl < OZ_S; ++sl) {
 #pragma unroll
@@ -418,18 +433,22 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z, con
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 oz_smem_addr(mbar + c % OZ_NBUF)));
+            }
+            __syncwarp();
         }
-        // chunk c - 1 frees the buffer chunk c + OZ_NBUF - 1 loads into
-        if (c >= 1) mine = wait_chunk(c - 1);
-        if (c + OZ_NBUF - 1 < nc && mine) load_chunk(c + OZ_NBUF - 1);
+        // chunk c - 2 (long done: the MMAs of chunks c - 1 and c stay queued)
+        // frees the buffer chunk c + OZ_NBUF - 2 loads into
+        if (c >= 2 && (!Z.tma || warp == 0)) mine = mine && wait_chunk(c - 2);
+        if (c + OZ_NBUF - 2 < nc && mine) load_chunk(c + OZ_NBUF - 2);
     }
-    if (ok) {
-        ok = __syncthreads_and(mine && wait_chunk(nc - 1)) != 0;
+    if (ok) {   // agree that every wait succeeded before waiting for the last chunk's MMAs
+        ok = __syncthreads_and(mine) != 0;
+        if (ok) ok = __syncthreads_and(wait_chunk(nc - 1)) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (ok) fold(nc - 1);
     }
     if (!ok && tid == 0) atomicExch(Z.err, 1);
-    if (!ok && Z.tma && tid == 0)   // boxes still in flight land before the CTA ends (bounded)
+    if (!ok && Z.tma && warp == 0)   // boxes still in flight land before the CTA ends (bounded)
         for (int c = consumed; c < issued; ++c) oz_wait(full + c % OZ_NBUF, (uint32_t)((c / OZ_NBUF) & 1));
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
