@@ -84,7 +84,9 @@ __device__ __forceinline__ ChildRef child_ref(const MergeLevelDev &L, int child)
 
 // Scale exponent e with |x| < 2^e for every |x| <= amax, from the bits of
 // amax (0 for amax == 0 or subnormal: such rows are flushed; OZ_NONFINITE
-// for inf / NaN, which the epilogue turns into NaN).
+// for inf, and the slicing kernels give it to any row / column holding a
+// NaN or inf; the epilogue writes NaN where a row's or column's scale is
+// OZ_NONFINITE).
 constexpr int OZ_NONFINITE = 4096;
 __device__ __forceinline__ int oz_exp(double amax) {
     const int ex = (int)(((unsigned long long)__double_as_longlong(amax) >> 52) & 0x7FF);
@@ -154,10 +156,15 @@ __global__ void __launch_bounds__(256) oz_slice_a(OzJob J, OzakiScratch Z) {
             tr = J.a + (long long)s * J.sa + (long long)P * J.lda;
         }
         double mx = 0.0;
-        for (int k = lane; k < J.K; k += 32) mx = fmax(mx, fabs(tr[s3 ? s3[k] : k]));
+        bool bad = false;   // fmax drops NaN: non-finite entries are flagged on their own
+        for (int k = lane; k < J.K; k += 32) {
+            const double v = tr[s3 ? s3[k] : k];
+            mx = fmax(mx, fabs(v));
+            bad |= !isfinite(v);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        e = oz_exp(mx);
+        e = __any_sync(0xffffffffu, bad) ? OZ_NONFINITE : oz_exp(mx);
     }
     for (int g = lane; g < Z.Kp / 8; g += 32) {
         double x[8];
@@ -176,11 +183,16 @@ __global__ void __launch_bounds__(256) oz_colexp_b(OzJob J, OzakiScratch Z) {
     const int s = blockIdx.y, c = blockIdx.x * 256 + threadIdx.x;
     if (c >= Z.Np) return;
     double mx = 0.0;
+    bool bad = false;   // fmax drops NaN: non-finite entries are flagged on their own
     if (c < J.N) {
         const double *b = J.b + (long long)s * J.sb + c;
-        for (int k = 0; k < J.K; ++k) mx = fmax(mx, fabs(b[(long long)k * J.ldb]));
+        for (int k = 0; k < J.K; ++k) {
+            const double v = b[(long long)k * J.ldb];
+            mx = fmax(mx, fabs(v));
+            bad |= !isfinite(v);
+        }
     }
-    Z.Fb[(long long)s * Z.Np + c] = oz_exp(mx);
+    Z.Fb[(long long)s * Z.Np + c] = bad ? OZ_NONFINITE : oz_exp(mx);
 }
 
 // B slices Bs[t][c][k] (K-contiguous) from a 64 (k) x 32 (c) shared tile;

@@ -290,3 +290,22 @@ def test_parent_maps_on_tensor_cores_match_fp64_pipe():
     assert float((th1 - th0).norm() / th0.norm()) < 1e-13
     assert float((u1 - u0).norm() / u0.norm()) < 1e-12
     plan.close()
+
+
+def test_nonfinite_leaf_map_reaches_the_root_on_both_paths():
+    """A NaN in one leaf's T reaches the root map on both paths: the
+    tensor-core products mark the rows and columns holding a non-finite
+    value NaN (their integer slices cannot carry it), as the FP64 pipe
+    propagates it; the call returns normally."""
+    w = WL.bumps(p=12, nx=8, ny=8, kappa=20.0, seed=5, m=1)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    out = plan.condense(coef, f, m=1)
+    T = out["T"].clone()
+    T[5] = float("nan")   # leaf 0, row 0, column 5
+    for tensor in (True, False):
+        plan.set_merge_tensor(tensor)
+        th = plan.merge_boxes(8, 8, 1, 1, T, out["h"], 1, root=True)
+        torch.cuda.synchronize()
+        assert torch.isnan(th).any(), tensor
+    plan.close()
