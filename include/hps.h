@@ -53,8 +53,9 @@ typedef enum {
     HPS_ERR_ARG = 1,      /* invalid argument; nothing was enqueued */
     HPS_ERR_CUDA = 2,     /* a CUDA runtime call failed (message in hps_last_error) */
     HPS_ERR_OOM = 3,      /* device workspace could not be allocated */
-    HPS_ERR_SINGULAR = 4, /* reserved for host-side checks of info[] */
-    HPS_ERR_NOCONV = 5,   /* reserved for host-side checks of info[] */
+    HPS_ERR_SINGULAR = 4, /* an exact zero pivot: hps_check_info on a leaf's info > 0,
+                             hps_merge / hps_merge_boxes on a merge's Z */
+    HPS_ERR_NOCONV = 5,   /* hps_check_info: a mixed-precision leaf did not converge */
     HPS_ERR_STATE = 6     /* call out of order (e.g. hps_solve before hps_merge) */
 } hps_status;
 
@@ -360,6 +361,16 @@ hps_status hps_set_refine_stop(hps_plan *plan, int residual);
  * FP64; waits for the stream of that call. */
 hps_status hps_fallback_count(hps_plan *plan, int *count);
 
+/* Host-side check of a device info[] array of n entries (as hps_condense,
+ * hps_iti_condense and hps_leaf_resolve write it), after the stream that
+ * wrote it (synchronous copy on the legacy stream).  Returns HPS_OK when
+ * every entry is 0, HPS_ERR_SINGULAR when some entry is > 0 (exact zero
+ * pivot), else HPS_ERR_NOCONV when some entry is < 0 (refinement did not
+ * reach tol); *first (may be NULL) receives the index of the first entry
+ * of that kind, -1 for HPS_OK.  plan may be NULL (the message then goes to
+ * hps_last_error(NULL)).  HPS_ERR_ARG for n < 0 or a NULL array with n > 0. */
+hps_status hps_check_info(hps_plan *plan, const int *d_info, int n, int *first);
+
 /* Kernel timing with CUDA events recorded on the launch stream around the
  * condensation kernel of every hps_condense call.  hps_set_timing(plan, 1)
  * enables it and clears the record; hps_phase_times fills up to n values:
@@ -411,7 +422,7 @@ void hps_destroy(hps_plan *plan);
 
 /* ABI version: major * 100 + minor (1.01: hps_merge_boxes, hps_solve_boxes;
  * 1.02: hps_slab_factor, hps_slab_solve; 1.03: hps_iti_condense;
- * 1.04: hps_set_merge_tensor). */
+ * 1.04: hps_set_merge_tensor; 1.05: hps_check_info). */
 int hps_version(void);
 
 #ifdef __cplusplus

@@ -186,7 +186,7 @@ struct hps_plan {
 
 extern "C" {
 
-int hps_version(void) { return 104; }
+int hps_version(void) { return 105; }
 
 const char *hps_last_error(const hps_plan *plan) {
     if (plan == nullptr) return g_build_error.c_str();
@@ -673,6 +673,36 @@ hps_status hps_set_refine_stop(hps_plan *P, int residual) {
     return HPS_OK;
 }
 
+hps_status hps_check_info(hps_plan *P, const int *d_info, int n, int *first) {
+    auto fail = [&](hps_status st, const std::string &msg) {
+        if (P) return P->fail(st, msg);
+        g_build_error = msg;
+        return st;
+    };
+    if (first) *first = -1;
+    if (n < 0 || (n > 0 && d_info == nullptr)) return fail(HPS_ERR_ARG, "hps_check_info: n >= 0 and d_info required");
+    if (n == 0) return HPS_OK;
+    std::vector<int> info((size_t)n);
+    cudaError_t e = cudaMemcpy(info.data(), d_info, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(HPS_ERR_CUDA, std::string("hps_check_info: ") + cudaGetErrorString(e));
+    int pos = -1, neg = -1;
+    for (int i = 0; i < n && pos < 0; ++i) {
+        if (info[i] > 0) pos = i;
+        else if (info[i] < 0 && neg < 0) neg = i;
+    }
+    if (pos >= 0) {
+        if (first) *first = pos;
+        return fail(HPS_ERR_SINGULAR, "hps_check_info: entry " + std::to_string(pos) + " has an exact zero pivot at step " +
+                                          std::to_string(info[pos]));
+    }
+    if (neg >= 0) {
+        if (first) *first = neg;
+        return fail(HPS_ERR_NOCONV, "hps_check_info: entry " + std::to_string(neg) + " did not converge in " +
+                                        std::to_string(-info[neg]) + " corrections");
+    }
+    return HPS_OK;
+}
+
 hps_status hps_fallback_count(hps_plan *P, int *count) {
     if (P == nullptr || count == nullptr) return HPS_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(count, P->d_queue + 1, sizeof(int), cudaMemcpyDeviceToHost, P->last_stream);
@@ -910,6 +940,17 @@ static hps_status merge_tree(hps_plan *P, const char *who, int nx, int ny, int w
         e = cudaMemcpyAsync(&flag, P->oz_err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess && flag) return P->fail(HPS_ERR_CUDA, std::string(who) + ": a tensor-core wait timed out");
+    }
+    // an exactly singular Z (zero pivot) leaves inf / NaN in the maps: say where
+    for (size_t li = 0; li < hl.size() && e == cudaSuccess; ++li) {
+        std::vector<int> info((size_t)hl[li].nm);
+        e = cudaMemcpyAsync(info.data(), P->levels[li].info.p, info.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (size_t k = 0; k < info.size() && e == cudaSuccess; ++k)
+            if (info[k] > 0)
+                return P->fail(HPS_ERR_SINGULAR, std::string(who) + ": level " + std::to_string(li) + ", merge " +
+                                                     std::to_string(k) + ": exact zero pivot in Z at step " +
+                                                     std::to_string(info[k]));
     }
     if (e != cudaSuccess) return P->cuda_fail(e, who);
     if ((e = P->u_leaf.ensure((size_t)P->n_leaves * nbc0 * std::max(m, 1) * sizeof(double))) != cudaSuccess)

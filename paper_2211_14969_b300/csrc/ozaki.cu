@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(OZ_NT, 1) oz_gemm(OzJob J, OzakiScratch Z, con
             if (!cv[u]) continue;
             const int c = u * 32 + lane, sc = ea + fb[u];
             double v;
-            if (sc >= OZ_NONFINITE) v = __longlong_as_double(0x7FF8000000000000LL);
+            if (ea >= OZ_NONFINITE || fb[u] >= OZ_NONFINITE) v = __longlong_as_double(0x7FF8000000000000LL);
             else v = fma(sign, oz_scaled_i64(stX[r * SLD + c], sc - 49) + oz_scaled_f32(stT[r * SLD + c], sc - 56), gv[i][u]);
             out[c] = v;
         }

@@ -68,6 +68,7 @@ def load_library():
     L.hps_set_merge_tensor.argtypes = [vp, i]
     L.hps_set_merge_split.argtypes = [vp, i]
     L.hps_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.hps_check_info.argtypes = [vp, vp, i, ctypes.POINTER(ctypes.c_int)]
     L.hps_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     L.hps_last_launch_count.argtypes = [vp]
     L.hps_last_error.argtypes = [vp]
@@ -78,7 +79,7 @@ def load_library():
     for name in ("hps_build_leaves", "hps_leaf_nodes", "hps_condense", "hps_condense_host", "hps_merge", "hps_solve",
                  "hps_merge_boxes", "hps_solve_boxes", "hps_slab_factor", "hps_slab_solve", "hps_iti_condense",
                  "hps_set_timing", "hps_set_blocking", "hps_set_fp64_fallback", "hps_set_merge_split", "hps_set_refine_stop", "hps_set_merge_tensor",
-                 "hps_fallback_count",
+                 "hps_fallback_count", "hps_check_info",
                  "hps_phase_times", "hps_last_launch_count"):
         getattr(L, name).restype = i
     _lib = L
@@ -244,6 +245,22 @@ class Plan:
     def set_merge_split(self, below=-1):
         """Levels with fewer than `below` merges solve over many CTAs (-1: SM count; 0: never)."""
         self.check(load_library().hps_set_merge_split(self.handle, int(below)), "hps_set_merge_split")
+
+    def check_info(self, info):
+        """Host-side check of a device info tensor (hps_check_info): None when
+        every entry is 0, else (status name, index of the first offending
+        entry): 'HPS_ERR_SINGULAR' (exact zero pivot) before
+        'HPS_ERR_NOCONV' (refinement did not converge)."""
+        import torch
+        if not (info.is_cuda and info.dtype == torch.int32 and info.is_contiguous()):
+            raise ValueError("info must be a contiguous int32 CUDA tensor")
+        first = ctypes.c_int()
+        st = load_library().hps_check_info(self.handle, _ptr(info), int(info.numel()), ctypes.byref(first))
+        if st == HPS_OK:
+            return None
+        if st in (HPS_ERR_SINGULAR, HPS_ERR_NOCONV):
+            return STATUS[st], first.value
+        self.check(st, "hps_check_info")
 
     def fallback_count(self):
         n = ctypes.c_int()

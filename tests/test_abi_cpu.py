@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert lib.hps_version() == 104
+    assert lib.hps_version() == 105
 
 
 def _build(lib, p, boxes, kappa=1.0, out=True):

@@ -293,19 +293,39 @@ def test_parent_maps_on_tensor_cores_match_fp64_pipe():
 
 
 def test_nonfinite_leaf_map_reaches_the_root_on_both_paths():
-    """A NaN in one leaf's T reaches the root map on both paths: the
-    tensor-core products mark the rows and columns holding a non-finite
-    value NaN (their integer slices cannot carry it), as the FP64 pipe
-    propagates it; the call returns normally."""
+    """A NaN in leaf 0's T at (its west node 0, its north node 0), p = 12,
+    8 x 8 leaves: at the second level the north node is on the shared edge
+    (20 nodes, a tensor-core product), so the NaN sits in the left factor's
+    row of the outer-boundary node; that row of every parent map, and of
+    the root map, must be NaN on both paths (the integer slices cannot
+    carry a NaN: the row's scale marks it), Z stays finite, and the NaN
+    patterns of the two paths agree."""
     w = WL.bumps(p=12, nx=8, ny=8, kappa=20.0, seed=5, m=1)
     plan = hps.Plan(w.p, w.boxes(), w.kappa)
     coef, f, _ = gpu_inputs(w, plan)
     out = plan.condense(coef, f, m=1)
     T = out["T"].clone()
-    T[5] = float("nan")   # leaf 0, row 0, column 5
+    T[30] = float("nan")   # leaf 0 (40 edge nodes [W, E, S, N]): row 0 (west), column 30 (north)
+    pattern = {}
     for tensor in (True, False):
         plan.set_merge_tensor(tensor)
         th = plan.merge_boxes(8, 8, 1, 1, T, out["h"], 1, root=True)
         torch.cuda.synchronize()
-        assert torch.isnan(th).any(), tensor
+        pattern[tensor] = torch.isnan(th)
+        assert pattern[tensor].any(), tensor
+    assert torch.equal(pattern[True], pattern[False])
+    plan.close()
+
+
+def test_check_info_codes():
+    """hps_check_info on device info arrays: success, an exact zero pivot
+    (reported before a non-converged entry), a non-converged entry alone."""
+    w = WL.planewave(p=6, nx=2, ny=2)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    mk = lambda v: torch.tensor(v, dtype=torch.int32, device="cuda")
+    assert plan.check_info(mk([0, 0, 0])) is None
+    assert plan.check_info(mk([0, -3, 7, 0])) == ("HPS_ERR_SINGULAR", 2)
+    assert plan.check_info(mk([0, 0, -8])) == ("HPS_ERR_NOCONV", 2)
+    with pytest.raises(ValueError):
+        plan.check_info(torch.zeros(3, dtype=torch.float64, device="cuda"))
     plan.close()
