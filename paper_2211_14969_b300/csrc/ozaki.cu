@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "hps_internal.cuh"
@@ -583,12 +584,15 @@ typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, 
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// the driver's tensor-map encoder, through the runtime (null if unavailable:
-// the GEMM then loads with cp.async)
+// the driver's tensor-map encoder, through the runtime (null if unavailable,
+// or when the environment sets HPS_OZAKI_TMA=0: the GEMM then loads with
+// cp.async); looked up once per process
 static EncodeTiled encode_tiled() {
     static EncodeTiled fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
+        const char *env = getenv("HPS_OZAKI_TMA");
+        if (env && env[0] == '0') return;
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&

@@ -329,3 +329,41 @@ def test_check_info_codes():
     with pytest.raises(ValueError):
         plan.check_info(torch.zeros(3, dtype=torch.float64, device="cuda"))
     plan.close()
+
+
+_CPASYNC_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[2])
+from gpu_cases import gpu_inputs
+from paper_2211_14969_b300 import hps
+from paper_2211_14969_b300 import workloads as WL
+w = WL.bumps(p=20, nx=16, ny=16, kappa=60.0, seed=4, m=1)
+plan = hps.Plan(w.p, w.boxes(), w.kappa)
+coef, f, _ = gpu_inputs(w, plan)
+out = plan.condense(coef, f, m=1)
+th = plan.merge_boxes(16, 16, 1, 1, out["T"], out["h"], 1, root=True)
+np.save(sys.argv[1], th.cpu().numpy())
+"""
+
+
+def test_tensor_core_loads_by_cp_async_match_tma(tmp_path):
+    """The tensor-core products load their operands as TMA boxes where the
+    driver encodes tensor maps, else by cp.async of the same runs
+    (HPS_OZAKI_TMA=0 forces the latter, read once per process): the root
+    map of a 16 x 16, p = 20 merge from a child process on cp.async equals
+    this process's, bit for bit."""
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    root = os.path.dirname(here)
+    path = str(tmp_path / "th_cpasync.npy")
+    env = dict(os.environ, HPS_OZAKI_TMA="0", PYTHONPATH=os.pathsep.join([root, here]))
+    subprocess.run([sys.executable, "-c", _CPASYNC_CHILD, path, here], check=True, env=env, cwd=root, timeout=600)
+    w = WL.bumps(p=20, nx=16, ny=16, kappa=60.0, seed=4, m=1)
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    out = plan.condense(coef, f, m=1)
+    th = plan.merge_boxes(16, 16, 1, 1, out["T"], out["h"], 1, root=True).cpu().numpy()
+    assert np.array_equal(np.load(path), th)
+    plan.close()
