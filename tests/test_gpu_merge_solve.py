@@ -367,3 +367,22 @@ def test_tensor_core_loads_by_cp_async_match_tma(tmp_path):
     th = plan.merge_boxes(16, 16, 1, 1, out["T"], out["h"], 1, root=True).cpu().numpy()
     assert np.array_equal(np.load(path), th)
     plan.close()
+
+
+@pytest.mark.parametrize("m", [0, 3])
+def test_tensor_core_merge_load_columns(m):
+    """No body loads (the parents' maps without h columns) and three load
+    columns: the root [T | h] of a 16 x 16, p = 20 merge with the
+    tensor-core products against the FP64 pipe."""
+    w = WL.bumps(p=20, nx=16, ny=16, kappa=60.0, seed=9, m=max(m, 1))
+    w.m = m
+    plan = hps.Plan(w.p, w.boxes(), w.kappa)
+    coef, f, _ = gpu_inputs(w, plan)
+    out = plan.condense(coef, f if m else None, m=m)
+    th = {}
+    for tensor in (True, False):
+        plan.set_merge_tensor(tensor)
+        th[tensor] = plan.merge_boxes(16, 16, 1, 1, out["T"], out["h"] if m else None, m, root=True).clone()
+        torch.cuda.synchronize()
+    assert float((th[True] - th[False]).norm() / th[False].norm()) < 1e-13
+    plan.close()
