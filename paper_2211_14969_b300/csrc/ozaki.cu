@@ -179,21 +179,32 @@ __global__ void __launch_bounds__(256) oz_slice_a(OzJob J, OzakiScratch Z) {
     if (lane == 0) Z.Ea[(long long)s * Z.Mp + P] = e;
 }
 
-// B column exponents over the K rows.
+// B column exponents over the K rows: 32 columns per block, each column's
+// rows split over the 8 warps (coalesced along the columns), then combined.
 __global__ void __launch_bounds__(256) oz_colexp_b(OzJob J, OzakiScratch Z) {
-    const int s = blockIdx.y, c = blockIdx.x * 256 + threadIdx.x;
-    if (c >= Z.Np) return;
+    __shared__ double smx[8][32];
+    __shared__ int sbad[8][32];
+    const int s = blockIdx.y, cc = threadIdx.x & 31, rs = threadIdx.x >> 5, c = blockIdx.x * 32 + cc;
     double mx = 0.0;
     bool bad = false;   // fmax drops NaN: non-finite entries are flagged on their own
     if (c < J.N) {
         const double *b = J.b + (long long)s * J.sb + c;
-        for (int k = 0; k < J.K; ++k) {
+        for (int k = rs; k < J.K; k += 8) {
             const double v = b[(long long)k * J.ldb];
             mx = fmax(mx, fabs(v));
             bad |= !isfinite(v);
         }
     }
-    Z.Fb[(long long)s * Z.Np + c] = bad ? OZ_NONFINITE : oz_exp(mx);
+    smx[rs][cc] = mx;
+    sbad[rs][cc] = bad;
+    __syncthreads();
+    if (rs == 0 && c < Z.Np) {
+        for (int r = 1; r < 8; ++r) {
+            mx = fmax(mx, smx[r][cc]);
+            bad |= sbad[r][cc] != 0;
+        }
+        Z.Fb[(long long)s * Z.Np + c] = bad ? OZ_NONFINITE : oz_exp(mx);
+    }
 }
 
 // B slices Bs[t][c][k] (K-contiguous) from a 64 (k) x 32 (c) shared tile;
@@ -607,7 +618,7 @@ cudaError_t launch_ozaki(const OzJob &J, const OzakiScratch &Z0, cudaStream_t st
     // the layout for this job's sizes, in the same scratch (sized for the largest job)
     OzakiScratch Z = ozaki_layout(Z0.As, J.nm, J.M, J.K, J.N, Z0.err);
     oz_slice_a<<<dim3((Z.Mp * 32 + 255) / 256, J.nm), 256, 0, st>>>(J, Z);
-    oz_colexp_b<<<dim3((Z.Np + 255) / 256, J.nm), 256, 0, st>>>(J, Z);
+    oz_colexp_b<<<dim3(Z.Np / 32, J.nm), 256, 0, st>>>(J, Z);
     oz_slice_b<<<dim3(Z.Np / 32, Z.Kp / 64, J.nm), 256, 0, st>>>(J, Z);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
